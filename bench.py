@@ -1,0 +1,386 @@
+"""Benchmark: k-core decomposition throughput on GB300.
+
+One step decomposes the workload graph completely with both methods of the
+library, PeelOne (Alg. 4) and HistoCore (Alg. 6), through the C ABI; each
+result is a full coreness vector. The metric is coreness edges/s: undirected
+edges decomposed per second, summed over the two decompositions of a step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the launching stream with an L2 flush (a 512 MiB write) before it, outside
+the events. Every method call is also bracketed by its own events, which give
+the per-kernel durations used for the roofline. With N > 1 (torchrun), each
+rank decomposes its own replica of the workload (the graphs are independent,
+there is no collective on the data path); value = all ranks' edges / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat24": "R-MAT scale 24, edge factor 16, a/b/c/d .57/.19/.19/.05, int32 CSR",
+    "rmat22": "R-MAT scale 22, edge factor 16, int64 row_ptr",
+    "rmat16": "R-MAT scale 16, edge factor 16, int32 CSR",
+    "chunglu24": "Chung-Lu beta 2.1, 2^24 vertices, mean degree 20, planted K_3000",
+    "grid4096": "4096 x 4096 4-neighbour grid",
+}
+# bounded CPU samples of each workload for the oracle timing (same recipe, smaller)
+CPU_SAMPLE = {"rmat24": "rmat22", "rmat22": "rmat20", "rmat16": "rmat16",
+              "chunglu24": "rmat22", "grid4096": "grid2048"}
+REF_SAMPLE = {"rmat24": "rmat20", "rmat22": "rmat19", "rmat16": "rmat16",
+              "chunglu24": "rmat20", "grid4096": "grid1024"}
+
+
+def make_graph(name, device):
+    import graphgen as gg
+    if name.startswith("grid") and name[4:].isdigit():
+        s = int(name[4:])
+        return gg.grid_graph(s, s, device)
+    if name in ("rmat16", "rmat22", "rmat24", "chunglu24", "grid4096"):
+        return gg.workload(name, device)
+    if name.startswith("rmat") and name[4:].isdigit():
+        return gg.rmat_graph(int(name[4:]), 16, gg.SEED_BASE + 3, device)
+    raise ValueError(name)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2402_15253_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, method: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (its `kernel_source_hash` line matches)."""
+    path = os.path.join(ROOT, "profiles", f"{method}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m1 = re.search(r"kernel_source_hash\s*=\s*`?([0-9a-f]+)", text)
+    m2 = re.search(r"dram_bytes_per_launch\s*=\s*`?([0-9.eE+]+)", text)
+    if not (m1 and m2) or m1.group(1) != kernel_source_hash():
+        return None
+    return float(m2.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_time(sample: str, repeats: int = 1):
+    """Single-threaded Batagelj-Zaversnik on a host copy of `sample`."""
+    import oracle
+    g = make_graph(sample, "cuda")
+    rp, ci = g.numpy()
+    del g
+    oracle.lib()   # load the library outside the timing
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.bz_coreness(rp, ci)
+        times.append(time.perf_counter() - t0)
+    edges = int(rp[-1]) // 2
+    return edges, statistics.median(times)
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    """The CPU oracle (single-threaded BZ), as it stands, on a bounded sample."""
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    sample = REF_SAMPLE.get(args.workload, "rmat20")
+    import torch  # noqa: F401  (graph generation runs through torch on the CPU here)
+    import graphgen as gg  # noqa: F401
+    import oracle
+    g = make_graph(sample, "cpu")
+    rp, ci = g.numpy()
+    del g
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle.bz_coreness(rp, ci)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.bz_coreness(rp, ci)
+    dt = time.perf_counter() - t0
+    edges = int(rp[-1]) // 2
+    value = edges * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "coreness edges/s", "value": value, "unit": "edges/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample, "step": "one BZ decomposition"},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample}: same recipe at reduced scale, "
+                                   f"{edges} undirected edges, single-threaded BZ"},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="pico", choices=["pico", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    import paper_2402_15253_gb300 as pico
+
+    g = make_graph(args.workload, dev)
+    n, arcs = g.n, g.arcs
+    m_und = arcs // 2
+    rp, ci = g.row_ptr, g.col_idx
+    w_r = rp.element_size()
+    out = {a: torch.empty(n, dtype=torch.int32, device=dev) for a in ("peelone", "histocore")}
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        for i, a in enumerate(("peelone", "histocore")):
+            if ev is not None:
+                ev[2 * i].record(stream)
+            rc = (pico.pico_coreness if w_r == 4 else pico.pico_coreness_i64)(
+                rp, ci, n, arcs, out[a], pico.ALGOS[a], stream)
+            if ev is not None:
+                ev[2 * i + 1].record(stream)
+            if rc != 0:
+                raise pico.PicoError(rc, a)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    st = pico.pico_last_device_status(stream)
+    if st != 0:
+        raise pico.PicoError(st, "warm-up")
+    stats = {}
+    for a in ("peelone", "histocore"):
+        pico.coreness(rp, ci, a, out=out[a])
+        stats[a] = pico.pico_get_stats(stream)
+    kmax = int(out["peelone"].max().item())
+    if not torch.equal(out["peelone"], out["histocore"]):
+        raise AssertionError("PeelOne and HistoCore disagree")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        for k in range(args.steps):
+            flush.zero_()
+            step_ev[k][0].record(stream)
+            step(evs[k])
+            step_ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    st = pico.pico_last_device_status(stream)
+    if st != 0:
+        raise pico.PicoError(st, "timed steps")
+
+    step_ms = [s.elapsed_time(e) for s, e in step_ev]
+    per = {a: [evs[k][2 * i].elapsed_time(evs[k][2 * i + 1]) for k in range(args.steps)]
+           for i, a in enumerate(("peelone", "histocore"))}
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = 2 * m_und * args.steps * ws
+    value = units / (total_ms / 1000.0)
+
+    # roofline of the dominant kernel: algorithm-neutral bytes B_min per launch
+    b_min = w_r * (n + 1) + 4 * arcs + 4 * arcs + 4 * n
+    peak, peak_kind = peaks()
+    mean_ms = {a: statistics.mean(v) for a, v in per.items()}
+    dom = max(mean_ms, key=mean_ms.get)
+    achieved = b_min / (mean_ms[dom] / 1000.0) / 1e9
+    traffic = recorded_traffic(args.workload, dom)
+    methods = {a: {"ms_mean": mean_ms[a], "ms_median": statistics.median(per[a]),
+                   "edges_per_s": m_und / (mean_ms[a] / 1000.0),
+                   "bmin_gbs": b_min / (mean_ms[a] / 1000.0) / 1e9,
+                   "bmin_frac_of_" + peak_kind: b_min / (mean_ms[a] / 1000.0) / 1e9 / peak,
+                   "stats": stats[a]} for a in per}
+
+    line = {
+        "metric": "coreness edges/s", "value": value, "unit": "edges/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": n,
+                   "arcs": arcs, "undirected_edges": m_und, "kmax": kmax,
+                   "step": "full decomposition by PeelOne and by HistoCore (2 x edges)",
+                   "l2": "inputs larger than L2 (col_idx %.2f GB) and a 512 MiB L2 flush "
+                         "before every step, outside its events" % (4 * arcs / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "bytes_per_launch": b_min, "peak_kind": peak_kind,
+                     "bytes_model": "B_min = w_r(n+1) + 8 B/arc + 4 B/vertex"},
+        "methods": methods,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the public API from pinned host buffers
+        h_rp = rp.cpu().pin_memory()
+        h_ci = ci.cpu().pin_memory()
+        h_out = {a: torch.empty(n, dtype=torch.int32).pin_memory() for a in out}
+        d_rp = torch.empty_like(rp)
+        d_ci = torch.empty_like(ci)
+        e_steps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            d_rp.copy_(h_rp, non_blocking=True)
+            d_ci.copy_(h_ci, non_blocking=True)
+            for a in out:
+                pico.coreness(d_rp, d_ci, a, out=out[a], check=False)
+                h_out[a].copy_(out[a], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        line["e2e"] = {"value": 2 * m_und * e_steps / (e_ms / 1000.0), "unit": "edges/s",
+                       "h2d_bytes_per_step": h_rp.numel() * w_r + h_ci.numel() * 4,
+                       "d2h_bytes_per_step": 2 * 4 * n, "steps": e_steps,
+                       "wall_s": time.perf_counter() - t0}
+        for a in out:
+            if not torch.equal(h_out[a], out["peelone"].cpu()):
+                raise AssertionError("e2e result differs")
+        del d_rp, d_ci
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sample = CPU_SAMPLE.get(args.workload, args.workload)
+        edges, secs = cpu_oracle_time(sample)
+        line["cpu_baseline"] = {"value": edges / secs, "unit": "edges/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{sample}: same recipe at reduced scale, {edges} "
+                                          f"undirected edges, one single-threaded "
+                                          f"Batagelj-Zaversnik run ({secs:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

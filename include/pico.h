@@ -1,0 +1,124 @@
+/*
+ * pico.h -- C ABI of the GB300 (sm_103a) k-core decomposition library.
+ *
+ * The library computes the coreness of every vertex of a simple undirected
+ * graph: core(v) is the largest k such that v belongs to the k-core, the
+ * maximal subgraph whose minimum degree is at least k; an isolated vertex has
+ * core 0 (Sec. I of "PICO: Accelerating All k-Core Paradigms on GPU").
+ * Two methods compute it and return identical vectors:
+ *   PICO_ALGO_PEELONE    PeelOne (Sec. III, Alg. 4): level-synchronous peel
+ *                        with the clamped decrement of Sec. III-B ("assertion")
+ *                        and the dynamic frontier of Sec. III-C.
+ *   PICO_ALGO_HISTOCORE  HistoCore (Sec. IV-B, Alg. 6): h-index iteration
+ *                        over per-vertex neighbour histograms, restricted to
+ *                        the vertices whose count fell below their estimate
+ *                        (Thm. 2).
+ *
+ * Graph layout (CSR, device memory, read only):
+ *   row_ptr  n + 1 offsets; row_ptr[0] == 0, non-decreasing;
+ *            row_ptr[n] == m == the number of ARCS (twice the undirected
+ *            edges: every edge {u, v} appears as u->v and v->u).
+ *   col_idx  m int32 neighbour ids in [0, n). The graph must be symmetric,
+ *            without self-loops or duplicate arcs. Neighbour order is free.
+ *   out_core n int32 results, written in full (device memory, caller-owned).
+ *
+ * Asynchrony: every compute call is enqueued on `stream` (NULL = the legacy
+ * default stream) and returns before the work is done. The return value
+ * reports argument and launch errors only. Failures seen on the device (a
+ * bounded wait that ran out, a malformed graph detected in flight) are
+ * recorded in a per-device status word: read it with pico_last_device_status
+ * after the call, which also synchronises the stream.
+ *
+ * Memory: scratch space comes from CUDA's stream-ordered allocator
+ * (cudaMallocAsync on `stream`) and is released on the same stream when the
+ * call's work ends; pico_workspace_bytes reports its size. Inputs are never
+ * written. Concurrent calls on different streams are independent, except
+ * that the per-device status word and statistics are shared (last writer wins).
+ *
+ * Requirements: a GPU of compute capability 10.3 (GB300); n < 2^31; for the
+ * int32-offset entry points m < 2^31. Thread safety: calls may come from any
+ * host thread; the CUDA device current on the calling thread is used.
+ */
+#ifndef PICO_H
+#define PICO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st *pico_stream_t;
+
+typedef enum {
+    PICO_ALGO_PEELONE = 0,   /* Alg. 4, Sec. III-C */
+    PICO_ALGO_HISTOCORE = 1  /* Alg. 6, Sec. IV-B */
+} pico_algo;
+
+typedef enum {
+    PICO_OK = 0,
+    PICO_ERR_INVALID_ARG = -1,   /* null pointer, negative size, unknown algo */
+    PICO_ERR_OOM = -2,           /* scratch allocation failed */
+    PICO_ERR_CUDA = -3,          /* a CUDA runtime call failed (launch, copy) */
+    PICO_ERR_NOT_CONVERGED = -4, /* a device loop exceeded its proven bound */
+    PICO_ERR_TIMEOUT = -5,       /* a device-side wait exceeded its time limit */
+    PICO_ERR_BAD_GRAPH = -6,     /* validation found a malformed CSR */
+    PICO_ERR_NO_DEVICE = -7      /* no usable sm_103 device is current */
+} pico_status;
+
+/*
+ * Coreness of one graph with int32 offsets (m < 2^31).
+ * n: vertices (>= 0); m: arcs (must equal row_ptr[n]); algo: a pico_algo.
+ * n == 0 is a no-op. Returns PICO_OK or a negative pico_status.
+ */
+int pico_coreness(const int32_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                  int32_t *out_core, int algo, pico_stream_t stream);
+
+/* The same with int64 offsets (row_ptr has n + 1 int64 entries). */
+int pico_coreness_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                      int32_t *out_core, int algo, pico_stream_t stream);
+
+/* Scratch bytes a single-graph call with these sizes allocates (admission
+   accounting). Returns 0 for invalid arguments. */
+size_t pico_workspace_bytes(int64_t n, int64_t m, int algo);
+
+/* Static text for a pico_status value (never NULL). */
+const char *pico_status_string(int status);
+
+/*
+ * Synchronises `stream`, then returns and clears the current device's sticky
+ * device-side status: PICO_OK, or the first error recorded by any call since
+ * the last read. Returns PICO_ERR_CUDA if the synchronisation itself fails.
+ */
+int pico_last_device_status(pico_stream_t stream);
+
+/* Counters of the most recent call on the current device (after a
+   synchronisation of its stream). Fields a method does not use stay 0. */
+typedef struct {
+    int64_t algo;        /* pico_algo of the call */
+    int64_t levels;      /* PeelOne: non-empty levels executed */
+    int64_t kmax;        /* PeelOne: largest level (the maximum coreness) */
+    int64_t subrounds;   /* PeelOne: frontier waves over all levels */
+    int64_t scans;       /* PeelOne: residual scans (levels + empty probes) */
+    int64_t rounds;      /* HistoCore: SumHisto/UpdateHisto rounds */
+    int64_t frontier;    /* HistoCore: sum over rounds of |V_cnt| */
+    int64_t barriers;    /* grid-wide barriers executed */
+    int64_t arcs;        /* adjacency entries read by the expansion phases */
+    int64_t atomics;     /* atomic read-modify-writes on core[] or histo[] */
+    int64_t slots;       /* HistoCore: histogram slots read by SumHisto */
+    int64_t blocks;      /* CTAs of the persistent launch */
+    int64_t reserved[4];
+} pico_stats;
+
+int pico_get_stats(pico_stream_t stream, pico_stats *out);
+
+/* Library version, as major * 10000 + minor * 100 + patch. */
+int pico_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PICO_H */

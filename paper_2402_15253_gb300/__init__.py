@@ -1,0 +1,166 @@
+"""Python binding of the pico C ABI (libpico.so, declared in include/pico.h).
+
+The functions named ``pico_*`` mirror the C entry points one to one and only
+marshal arguments: tensors become device pointers, streams become CUDA
+stream handles. :func:`coreness` is a convenience wrapper that allocates the
+output, picks the int32- or int64-offset entry point and raises on failure.
+Every step of the computation runs in the library's CUDA kernels; there is no
+CPU fallback, and importing this module fails if libpico.so is missing.
+
+Build the library with ``paper_2402_15253_gb300.build.build()`` (nvcc,
+sm_103a).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpico.so")
+
+PICO_ALGO_PEELONE = 0
+PICO_ALGO_HISTOCORE = 1
+ALGOS = {"peelone": PICO_ALGO_PEELONE, "histocore": PICO_ALGO_HISTOCORE}
+
+PICO_OK = 0
+PICO_ERR_INVALID_ARG = -1
+PICO_ERR_OOM = -2
+PICO_ERR_CUDA = -3
+PICO_ERR_NOT_CONVERGED = -4
+PICO_ERR_TIMEOUT = -5
+PICO_ERR_BAD_GRAPH = -6
+PICO_ERR_NO_DEVICE = -7
+
+
+class PicoError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {pico_status_string(status)} ({status})" if what
+                         else f"{pico_status_string(status)} ({status})")
+
+
+class pico_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "algo", "levels", "kmax", "subrounds", "scans", "rounds", "frontier", "barriers",
+        "arcs", "atomics", "slots", "blocks")] + [("reserved", ctypes.c_int64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libpico.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with paper_2402_15253_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.pico_coreness.argtypes = [vp, vp, i64, i64, vp, i32, vp]
+    L.pico_coreness_i64.argtypes = [vp, vp, i64, i64, vp, i32, vp]
+    L.pico_workspace_bytes.argtypes = [i64, i64, i32]
+    L.pico_workspace_bytes.restype = ctypes.c_size_t
+    L.pico_status_string.argtypes = [i32]
+    L.pico_status_string.restype = ctypes.c_char_p
+    L.pico_last_device_status.argtypes = [vp]
+    L.pico_get_stats.argtypes = [vp, ctypes.POINTER(pico_stats)]
+    for f in (L.pico_coreness, L.pico_coreness_i64, L.pico_last_device_status,
+              L.pico_get_stats, L.pico_version):
+        f.restype = i32
+    L.pico_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(None)
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    """None -> torch's current stream on the current device; an int is taken
+    as a raw cudaStream_t; torch.cuda.Stream objects are unwrapped."""
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# C ABI mirrors
+# ---------------------------------------------------------------------------
+
+def pico_coreness(row_ptr, col_idx, n: int, m: int, out_core, algo: int, stream=None) -> int:
+    return load().pico_coreness(_ptr(row_ptr), _ptr(col_idx), n, m, _ptr(out_core), algo,
+                                _stream(stream))
+
+
+def pico_coreness_i64(row_ptr, col_idx, n: int, m: int, out_core, algo: int, stream=None) -> int:
+    return load().pico_coreness_i64(_ptr(row_ptr), _ptr(col_idx), n, m, _ptr(out_core), algo,
+                                    _stream(stream))
+
+
+def pico_workspace_bytes(n: int, m: int, algo: int) -> int:
+    return int(load().pico_workspace_bytes(n, m, algo))
+
+
+def pico_status_string(status: int) -> str:
+    return load().pico_status_string(status).decode()
+
+
+def pico_last_device_status(stream=None) -> int:
+    return load().pico_last_device_status(_stream(stream))
+
+
+def pico_get_stats(stream=None) -> dict:
+    st = pico_stats()
+    rc = load().pico_get_stats(_stream(stream), ctypes.byref(st))
+    if rc != PICO_OK:
+        raise PicoError(rc, "pico_get_stats")
+    return st.as_dict()
+
+
+def pico_version() -> int:
+    return load().pico_version()
+
+
+# ---------------------------------------------------------------------------
+# convenience
+# ---------------------------------------------------------------------------
+
+def coreness(row_ptr: torch.Tensor, col_idx: torch.Tensor, algo="peelone",
+             out: torch.Tensor | None = None, stream=None, check: bool = True) -> torch.Tensor:
+    """Coreness of a CSR graph held in CUDA tensors (row_ptr int32 or int64,
+    col_idx int32). Returns an int32 tensor on the same device. With
+    ``check`` the stream is synchronised and device-side errors raise."""
+    a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    if not (row_ptr.is_cuda and col_idx.is_cuda):
+        raise ValueError("row_ptr and col_idx must be CUDA tensors")
+    if col_idx.dtype != torch.int32 or row_ptr.dtype not in (torch.int32, torch.int64):
+        raise TypeError("row_ptr must be int32/int64 and col_idx int32")
+    row_ptr = row_ptr.contiguous()
+    col_idx = col_idx.contiguous()
+    n = row_ptr.numel() - 1
+    m = col_idx.numel()
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int32, device=row_ptr.device)
+    with torch.cuda.device(row_ptr.device):
+        fn = pico_coreness if row_ptr.dtype == torch.int32 else pico_coreness_i64
+        rc = fn(row_ptr, col_idx, n, m, out, a, stream)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_coreness")
+        if check:
+            st = pico_last_device_status(stream)
+            if st != PICO_OK:
+                raise PicoError(st, "device")
+    return out

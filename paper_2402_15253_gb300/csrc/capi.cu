@@ -1,0 +1,206 @@
+// The C ABI declared in include/pico.h: argument checks, per-device state,
+// stream-ordered scratch allocation and dispatch to the persistent kernels.
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "pico.h"
+#include "pico_device.cuh"
+#include "pico_launch.h"
+
+namespace {
+
+struct DeviceState {
+    bool init = false;
+    pico::LaunchCfg cfg{};
+    pico::LastResult *last = nullptr;   // device memory
+};
+
+constexpr int kMaxDevices = 64;
+DeviceState g_dev[kMaxDevices];
+std::mutex g_mu;
+
+long long env_ll(const char *name, long long dflt)
+{
+    const char *s = std::getenv(name);
+    if (!s || !*s) return dflt;
+    char *end = nullptr;
+    long long v = std::strtoll(s, &end, 10);
+    return (end && *end == '\0' && v > 0) ? v : dflt;
+}
+
+// Per-device setup, done once per device by the first call on it (so the
+// first call should not be inside a stream capture).
+int device_state(DeviceState **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return PICO_ERR_NO_DEVICE;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    DeviceState &d = g_dev[dev];
+    if (!d.init) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return PICO_ERR_NO_DEVICE;
+        }
+        if (prop.major != 10 || prop.minor != 3 || !prop.cooperativeLaunch)
+            return PICO_ERR_NO_DEVICE;
+        d.cfg.device = dev;
+        d.cfg.sms = prop.multiProcessorCount;
+        d.cfg.max_blocks_per_sm = (int)env_ll("PICO_BLOCKS_PER_SM", 2);
+        d.cfg.limit_ns = (unsigned long long)env_ll("PICO_WAIT_LIMIT_MS", 4000) * 1000000ull;
+        if (cudaMalloc(&d.last, sizeof(pico::LastResult)) != cudaSuccess) {
+            cudaGetLastError();
+            return PICO_ERR_OOM;
+        }
+        if (cudaMemset(d.last, 0, sizeof(pico::LastResult)) != cudaSuccess) {
+            cudaGetLastError();
+            return PICO_ERR_CUDA;
+        }
+        // Keep freed scratch in this process's pool for the next call.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            unsigned long long keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+        d.init = true;
+    }
+    *out = &d;
+    return PICO_OK;
+}
+
+template <typename Off>
+int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_t *out,
+                  int algo, cudaStream_t stream)
+{
+    if (n < 0 || m < 0 || (algo != PICO_ALGO_PEELONE && algo != PICO_ALGO_HISTOCORE))
+        return PICO_ERR_INVALID_ARG;
+    if (n == 0) return PICO_OK;
+    if (!rp || !out || (m > 0 && !ci)) return PICO_ERR_INVALID_ARG;
+    if (n >= INT32_MAX) return PICO_ERR_INVALID_ARG;
+    if (sizeof(Off) == 4 && m >= INT32_MAX) return PICO_ERR_INVALID_ARG;
+    if (m >= (1ll << 36)) return PICO_ERR_INVALID_ARG;   // chunk lists use 32-bit indices
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    if (m == 0) {   // no arcs: every vertex is isolated
+        if (cudaMemsetAsync(out, 0, (size_t)n * sizeof(int32_t), stream) != cudaSuccess) {
+            cudaGetLastError();
+            return PICO_ERR_CUDA;
+        }
+        return PICO_OK;
+    }
+    const size_t bytes = algo == PICO_ALGO_PEELONE ? pico::peelone_ws_bytes(n, m)
+                                                   : pico::histocore_ws_bytes(n, m);
+    void *ws = nullptr;
+    if (cudaMallocAsync(&ws, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_OOM;
+    }
+    rc = algo == PICO_ALGO_PEELONE
+             ? pico::launch_peelone<Off>(rp, ci, n, m, out, ws, d->last, stream, d->cfg)
+             : pico::launch_histocore<Off>(rp, ci, n, m, out, ws, d->last, stream, d->cfg);
+    cudaFreeAsync(ws, stream);
+    if (rc != 0) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    return PICO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pico_coreness(const int32_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                  int32_t *out_core, int algo, pico_stream_t stream)
+{
+    return coreness_impl<int>(row_ptr, col_idx, n, m, out_core, algo, (cudaStream_t)stream);
+}
+
+int pico_coreness_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                      int32_t *out_core, int algo, pico_stream_t stream)
+{
+    return coreness_impl<long long>(reinterpret_cast<const long long *>(row_ptr), col_idx, n, m,
+                                    out_core, algo, (cudaStream_t)stream);
+}
+
+size_t pico_workspace_bytes(int64_t n, int64_t m, int algo)
+{
+    if (n < 0 || m < 0) return 0;
+    if (algo == PICO_ALGO_PEELONE) return pico::peelone_ws_bytes(n, m);
+    if (algo == PICO_ALGO_HISTOCORE) return pico::histocore_ws_bytes(n, m);
+    return 0;
+}
+
+const char *pico_status_string(int status)
+{
+    switch (status) {
+    case PICO_OK: return "ok";
+    case PICO_ERR_INVALID_ARG: return "invalid argument";
+    case PICO_ERR_OOM: return "out of device memory";
+    case PICO_ERR_CUDA: return "CUDA runtime error";
+    case PICO_ERR_NOT_CONVERGED: return "device loop exceeded its bound";
+    case PICO_ERR_TIMEOUT: return "device-side wait timed out";
+    case PICO_ERR_BAD_GRAPH: return "malformed graph";
+    case PICO_ERR_NO_DEVICE: return "no usable sm_103 device";
+    default: return "unknown status";
+    }
+}
+
+int pico_last_device_status(pico_stream_t stream)
+{
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    int st = 0;
+    if (cudaMemcpy(&st, &d->last->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(&d->last->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    return st;
+}
+
+int pico_get_stats(pico_stream_t stream, pico_stats *out)
+{
+    if (!out) return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    pico::LastResult h;
+    if (cudaMemcpy(&h, d->last, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->algo = h.algo;
+    out->levels = (int64_t)h.stats[pico::kStLevels];
+    out->kmax = (int64_t)h.stats[pico::kStKmax];
+    out->subrounds = (int64_t)h.stats[pico::kStSubrounds];
+    out->scans = (int64_t)h.stats[pico::kStScans];
+    out->rounds = (int64_t)h.stats[pico::kStRounds];
+    out->frontier = (int64_t)h.stats[pico::kStFrontier];
+    out->barriers = (int64_t)h.stats[pico::kStBarriers];
+    out->arcs = (int64_t)h.stats[pico::kStArcs];
+    out->atomics = (int64_t)h.stats[pico::kStAtomics];
+    out->slots = (int64_t)h.stats[pico::kStSlots];
+    out->blocks = (int64_t)h.stats[pico::kStBlocks];
+    return PICO_OK;
+}
+
+int pico_version(void) { return 100; }
+
+}  // extern "C"

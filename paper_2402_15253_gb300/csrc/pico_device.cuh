@@ -1,0 +1,456 @@
+// Device-side building blocks shared by the PeelOne and HistoCore kernels.
+//
+// * Ctrl: the per-call control block (grid barrier, status word, live
+//   counters and their per-barrier snapshots, statistics).
+// * grid_sync: a bounded grid-wide barrier for persistent cooperative
+//   launches. The last CTA to arrive copies the live counters into a snapshot
+//   before releasing the others, so every CTA sees the same counter values
+//   after the barrier. A CTA that waits longer than the time limit records
+//   PICO_ERR_TIMEOUT and returns false; every CTA returns false once any
+//   error is recorded, so an error ends the launch instead of hanging it.
+// * block_push2 / warp_push: aggregated appends to global lists (one atomic
+//   per block or per warp instead of one per element).
+// * expand: load-balanced traversal of the adjacency of a vertex list. Small
+//   vertices (degree <= kSmallDeg) are taken 32 at a time by a warp, which
+//   walks their concatenated neighbour lists with all lanes; large vertices
+//   are pre-split into chunks of kChunk arcs, one chunk per warp.
+#pragma once
+
+#include <cstdint>
+#include <climits>
+#include <cuda_runtime.h>
+
+namespace pico {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSmallDeg = 32;     // degree at or below which a vertex is "small"
+constexpr int kChunk = 1024;      // arcs per chunk of a large vertex
+constexpr int kThreads = 512;     // threads per CTA of the persistent kernels
+constexpr int kLiveWords = 32;
+
+enum : int {
+    kOk = 0,
+    kErrNotConverged = -4,
+    kErrTimeout = -5,
+    kErrBadGraph = -6,
+};
+
+struct alignas(128) Line {
+    unsigned w[32];
+};
+
+// Statistics slots (match pico_stats field order after `algo`).
+enum StatIdx : int {
+    kStLevels = 0, kStKmax, kStSubrounds, kStScans, kStRounds, kStFrontier,
+    kStBarriers, kStArcs, kStAtomics, kStSlots, kStBlocks, kStCount = 16
+};
+
+struct Ctrl {
+    Line bar;                 // w[0] arrivals, w[1] generation
+    Line stat;                // w[0] status, w[1] CTAs that finished
+    Line live;                // counters updated with atomics
+    Line snap[2];             // live counters as of the last barrier (by parity)
+    unsigned long long stats[kStCount];
+};
+
+// Per-device record of the most recent call, read by pico_get_stats and
+// pico_last_device_status.
+struct LastResult {
+    int status;               // sticky: first error since the last read
+    int pad;
+    long long algo;
+    unsigned long long stats[kStCount];
+};
+
+// ---------------------------------------------------------------------------
+// memory helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Mutable device data written by other CTAs is read through L2 only.
+__device__ __forceinline__ int ldcg(const int *p) { return __ldcg(p); }
+
+__device__ __forceinline__ void set_error(Ctrl *c, int code)
+{
+    atomicCAS(reinterpret_cast<int *>(&c->stat.w[0]), 0, code);
+}
+
+__device__ __forceinline__ int status_of(Ctrl *c)
+{
+    return ld_relaxed(reinterpret_cast<const int *>(&c->stat.w[0]));
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier with counter snapshot
+// ---------------------------------------------------------------------------
+// s_snap: shared memory, kLiveWords + 1 words; after the call s_snap[i] holds
+// the live counter i as of the barrier and s_snap[kLiveWords] the status.
+static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap, unsigned long long limit_ns)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned nblocks = gridDim.x;
+        unsigned gen = ld_acquire(&c->bar.w[1]);
+        __threadfence();
+        unsigned prev = atomicAdd(&c->bar.w[0], 1u);
+        if (prev == nblocks - 1) {
+            __threadfence();
+            unsigned *dst = c->snap[(gen + 1) & 1].w;
+            for (int i = 0; i < kLiveWords; ++i) dst[i] = ld_relaxed(&c->live.w[i]);
+            atomicExch(&c->bar.w[0], 0u);
+            __threadfence();
+            st_release(&c->bar.w[1], gen + 1);
+        } else {
+            const unsigned long long t0 = gtime();
+            unsigned spins = 0;
+            while (ld_acquire(&c->bar.w[1]) == gen) {
+                if ((++spins & 63) == 0) {
+                    if (status_of(c) != 0) break;
+                    if (gtime() - t0 > limit_ns) {
+                        set_error(c, kErrTimeout);
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        const unsigned *src = c->snap[(gen + 1) & 1].w;
+        for (int i = 0; i < kLiveWords; ++i) s_snap[i] = ld_relaxed(src + i);
+        s_snap[kLiveWords] = (unsigned)status_of(c);
+    }
+    __syncthreads();
+    return s_snap[kLiveWords] == 0;
+}
+
+// Called once by every CTA at the end of a persistent kernel: folds the CTA's
+// statistics into the call's control block; the last CTA publishes the
+// status and statistics to the per-device LastResult.
+__device__ __forceinline__ void finish_block(Ctrl *c, LastResult *last, int algo,
+                                             const unsigned long long *local, int nlocal)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < nlocal; ++i)
+            if (local[i]) atomicAdd(&c->stats[i], local[i]);
+        __threadfence();
+        unsigned done = atomicAdd(&c->stat.w[1], 1u);
+        if (done == gridDim.x - 1) {
+            __threadfence();
+            int st = status_of(c);
+            if (st != 0) atomicCAS(&last->status, 0, st);
+            last->algo = algo;
+            for (int i = 0; i < kStCount; ++i)
+                last->stats[i] = atomicAdd(&c->stats[i], 0ull);
+            last->stats[kStBlocks] = gridDim.x;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// aggregated appends
+// ---------------------------------------------------------------------------
+// Warp-aggregated append: all lanes of the warp call; lanes with `pred`
+// receive consecutive slots of *counter.
+__device__ __forceinline__ unsigned warp_push(unsigned *counter, bool pred)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned b = __ballot_sync(kFull, pred);
+    unsigned base = 0;
+    if (b) {
+        const int leader = __ffs(b) - 1;
+        if ((int)lane == leader) base = atomicAdd(counter, (unsigned)__popc(b));
+        base = __shfl_sync(kFull, base, leader);
+    }
+    return base + __popc(b & ((1u << lane) - 1u));
+}
+
+// Block-aggregated append to two lists at once. Every thread of the CTA must
+// call it (block-uniform control flow). s: shared scratch of >= 128 words.
+__device__ __forceinline__ void block_push2(bool p0, bool p1, unsigned *c0, unsigned *c1,
+                                            unsigned &pos0, unsigned &pos1, unsigned *s)
+{
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned b0 = __ballot_sync(kFull, p0), b1 = __ballot_sync(kFull, p1);
+    const unsigned lt = (1u << lane) - 1u;
+    if (lane == 0) {
+        s[warp] = __popc(b0);
+        s[32 + warp] = __popc(b1);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned x0 = lane < nw ? s[lane] : 0u, x1 = lane < nw ? s[32 + lane] : 0u;
+        unsigned i0 = x0, i1 = x1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y0 = __shfl_up_sync(kFull, i0, o), y1 = __shfl_up_sync(kFull, i1, o);
+            if ((int)lane >= o) {
+                i0 += y0;
+                i1 += y1;
+            }
+        }
+        const unsigned t0 = __shfl_sync(kFull, i0, 31), t1 = __shfl_sync(kFull, i1, 31);
+        unsigned base0 = 0, base1 = 0;
+        if (lane == 0) {
+            if (t0) base0 = atomicAdd(c0, t0);
+            if (t1) base1 = atomicAdd(c1, t1);
+        }
+        base0 = __shfl_sync(kFull, base0, 0);
+        base1 = __shfl_sync(kFull, base1, 0);
+        if (lane < nw) {
+            s[64 + lane] = base0 + i0 - x0;
+            s[96 + lane] = base1 + i1 - x1;
+        }
+    }
+    __syncthreads();
+    pos0 = s[64 + warp] + __popc(b0 & lt);
+    pos1 = s[96 + warp] + __popc(b1 & lt);
+    __syncthreads();
+}
+
+// Block-wide minimum folded into *target with one atomicMin per CTA.
+__device__ __forceinline__ void block_min_to(int v, int *target, int *s)
+{
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = __reduce_min_sync(kFull, v);
+    if (lane == 0) s[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < nw ? s[lane] : INT_MAX;
+        x = __reduce_min_sync(kFull, x);
+        if (lane == 0 && x != INT_MAX) atomicMin(target, x);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// load-balanced adjacency expansion
+// ---------------------------------------------------------------------------
+// Appends the chunk entries of a large vertex (degree d > kSmallDeg).
+__device__ __forceinline__ bool push_chunks(int v, long long d, int2 *list, unsigned *counter,
+                                            unsigned cap)
+{
+    const unsigned nch = (unsigned)((d + kChunk - 1) / kChunk);
+    const unsigned pos = atomicAdd(counter, nch);
+    if ((unsigned long long)pos + nch > cap) return false;
+    for (unsigned c = 0; c < nch; ++c) list[pos + c] = make_int2(v, (int)c);
+    return true;
+}
+
+// Functor interface used by expand():
+//   void item(int v, int &a, int &b)     per-vertex prologue (lane-local)
+//   void arc(bool valid, int v, int u, Off e, Off rs, int a, int b)
+//                                        called by ALL 32 lanes together;
+//                                        e is the arc index, rs = row_ptr[v]
+// `small` lists small vertices (nullptr: the identity list 0..nsmall-1, where
+// vertices with degree > kSmallDeg are skipped because their chunks are in
+// `big`). `big` lists (vertex, chunk) pairs.
+template <typename Off, typename F>
+__device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__restrict__ ci,
+                                       const int *small, unsigned nsmall, const int2 *big,
+                                       unsigned nbig, unsigned gwarp, unsigned nwarps, F &f)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned nbatch = (nsmall + 31u) / 32u;
+    const unsigned total = nbatch + nbig;
+    for (unsigned unit = gwarp; unit < total; unit += nwarps) {
+        if (unit < nbatch) {
+            const unsigned idx = unit * 32u + lane;
+            int v = -1, d = 0, a = 0, b = 0;
+            Off rs = 0;
+            if (idx < nsmall) {
+                v = small ? ldcg(small + idx) : (int)idx;
+                rs = rp[v];
+                const Off dd = rp[v + 1] - rs;
+                if (dd <= kSmallDeg) {
+                    d = (int)dd;
+                    if (d > 0) f.item(v, a, b);
+                }
+            }
+            int incl = d;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int excl = incl - d;
+            const int T = __shfl_sync(kFull, incl, 31);
+            for (int base = 0; base < T; base += 32) {
+                const int fidx = base + lane;
+                int o = 0;
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) {
+                    const int ex = __shfl_sync(kFull, excl, o + s);
+                    if (ex <= fidx) o += s;
+                }
+                const int vo = __shfl_sync(kFull, v, o);
+                const Off rso = __shfl_sync(kFull, rs, o);
+                const int exo = __shfl_sync(kFull, excl, o);
+                const int ao = __shfl_sync(kFull, a, o);
+                const int bo = __shfl_sync(kFull, b, o);
+                const bool valid = fidx < T;
+                const Off e = rso + (fidx - exo);
+                const int u = valid ? __ldg(ci + e) : -1;
+                f.arc(valid, vo, u, e, rso, ao, bo);
+            }
+        } else {
+            const int2 ent = __ldcg(big + (unit - nbatch));   // written by other CTAs
+            const int v = ent.x;
+            const Off rs = rp[v], re = rp[v + 1];
+            const Off s = rs + (Off)ent.y * kChunk;
+            const Off t = (s + kChunk < re) ? s + kChunk : re;
+            int a = 0, b = 0;
+            f.item(v, a, b);
+            for (Off e0 = s; e0 < t; e0 += 32) {
+                const Off e = e0 + lane;
+                const bool valid = e < t;
+                const int u = valid ? __ldg(ci + e) : -1;
+                f.arc(valid, v, u, e, rs, a, b);
+            }
+        }
+    }
+}
+
+}  // namespace pico
+
+namespace pico {
+
+// Block-wide maximum folded into *target with one atomicMax per CTA.
+__device__ __forceinline__ void block_max_to(unsigned v, unsigned *target, unsigned *s)
+{
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = __reduce_max_sync(kFull, v);
+    if (lane == 0) s[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned x = lane < nw ? s[lane] : 0u;
+        x = __reduce_max_sync(kFull, x);
+        if (lane == 0 && x != 0u) atomicMax(target, x);
+    }
+    __syncthreads();
+}
+
+// Block-wide sum of a per-thread counter, added to *target by thread 0.
+__device__ __forceinline__ void block_sum_to(unsigned long long v, unsigned long long *target,
+                                             unsigned long long *s)
+{
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) s[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (unsigned w = 0; w < nw; ++w) t += s[w];
+        if (t) atomicAdd(target, t);
+    }
+    __syncthreads();
+}
+
+}  // namespace pico
+
+namespace pico {
+
+// Block-aggregated append to N lists at once (generalises block_push2).
+// Every thread of the CTA must call it. s: shared scratch of >= 64 * N words.
+template <int N>
+__device__ __forceinline__ void block_pushN(const bool (&p)[N], unsigned *const (&ctr)[N],
+                                            unsigned (&pos)[N], unsigned *s)
+{
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned b[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        b[j] = __ballot_sync(kFull, p[j]);
+        if (lane == 0) s[32 * j + warp] = __popc(b[j]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const unsigned x = lane < nw ? s[32 * j + lane] : 0u;
+            unsigned inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(kFull, inc, o);
+                if ((int)lane >= o) inc += y;
+            }
+            const unsigned t = __shfl_sync(kFull, inc, 31);
+            unsigned base = 0;
+            if (lane == 0 && t) base = atomicAdd(ctr[j], t);
+            base = __shfl_sync(kFull, base, 0);
+            if (lane < nw) s[32 * (N + j) + lane] = base + inc - x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < N; ++j) pos[j] = s[32 * (N + j) + warp] + __popc(b[j] & lt);
+    __syncthreads();
+}
+
+// Block-aggregated allocation of `cnt` consecutive slots per thread from
+// *counter (one atomic per CTA). Returns this thread's first slot.
+__device__ __forceinline__ unsigned block_alloc(unsigned cnt, unsigned *counter, unsigned *s)
+{
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(kFull, inc, o);
+        if ((int)lane >= o) inc += y;
+    }
+    if (lane == 31) s[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned x = lane < nw ? s[lane] : 0u;
+        unsigned wi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(kFull, wi, o);
+            if ((int)lane >= o) wi += y;
+        }
+        const unsigned t = __shfl_sync(kFull, wi, 31);
+        unsigned base = 0;
+        if (lane == 0 && t) base = atomicAdd(counter, t);
+        base = __shfl_sync(kFull, base, 0);
+        if (lane < nw) s[32 + lane] = base + wi - x;
+    }
+    __syncthreads();
+    const unsigned r = s[32 + warp] + inc - cnt;
+    __syncthreads();
+    return r;
+}
+
+}  // namespace pico

@@ -1,0 +1,52 @@
+// Host-side interface between the C ABI (capi.cu) and the kernel translation
+// units. Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pico {
+
+struct LastResult;
+
+// Launch geometry of the persistent kernels for the current device.
+struct LaunchCfg {
+    int device;
+    int sms;                       // streaming multiprocessors
+    int max_blocks_per_sm;         // cap on co-resident CTAs per SM
+    unsigned long long limit_ns;   // time limit of every device-side wait
+};
+
+// Sub-buffer carving of a scratch allocation (256-byte aligned pieces).
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += count * sizeof(T);
+        return p;
+    }
+    size_t size() const { return (off + 255) & ~size_t(255); }
+};
+
+// Capacity of the list of (vertex, chunk) entries of large vertices: every
+// vertex of degree > kSmallDeg contributes ceil(deg / kChunk) entries.
+size_t chunk_capacity(long long m);
+
+size_t peelone_ws_bytes(long long n, long long m);
+size_t histocore_ws_bytes(long long n, long long m);
+
+template <typename Off>
+int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *core,
+                   void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
+
+template <typename Off>
+int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int *core,
+                     void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
+
+}  // namespace pico

@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
+
+Coreness is a unique integer vector, so every comparison is exact (bit for
+bit). The renditions of Alg. 4 and Alg. 6 in the oracle also fix the
+iteration structure: the GPU's non-empty levels, frontier waves and
+HistoCore rounds must equal theirs.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from conftest import load_g1
+
+pytestmark = pytest.mark.gpu
+
+ALGOS = ("peelone", "histocore")
+
+
+@pytest.fixture(scope="module")
+def pico():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_15253_gb300 as p
+    torch.cuda.set_device(0)
+    return p
+
+
+def run(pico, g, algo, off_dtype=None):
+    rp = g.row_ptr.cuda()
+    if off_dtype is not None:
+        rp = rp.to(off_dtype)
+    out = pico.coreness(rp, g.col_idx.cuda(), algo)
+    return out.cpu().numpy(), pico.pico_get_stats()
+
+
+def assert_same(got, want, what):
+    if not np.array_equal(got, want):
+        bad = np.nonzero(got != want)[0]
+        raise AssertionError(f"{what}: {len(bad)} vertices differ, first {bad[:8].tolist()} "
+                             f"got {got[bad[:8]].tolist()} want {want[bad[:8]].tolist()}")
+
+
+# --------------------------------------------------------------------------
+# small exact cases
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_g1(pico, algo):
+    n, edges, want = load_g1()
+    got, st = run(pico, gg.from_edge_list(edges, n), algo)
+    assert got.tolist() == want
+    if algo == "peelone":
+        assert st["levels"] == 2 and st["kmax"] == 2 and st["subrounds"] == 3
+    else:
+        assert st["rounds"] == 1 and st["frontier"] == 2
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_every_graph_up_to_5_vertices(pico, algo):
+    """All labelled graphs on 1..5 vertices, as one disjoint union."""
+    parts, wants = [], []
+    for n in range(1, 6):
+        pairs = list(itertools.combinations(range(n), 2))
+        for mask in range(1 << len(pairs)):
+            edges = [pairs[i] for i in range(len(pairs)) if mask >> i & 1]
+            parts.append(gg.from_edge_list(edges, n))
+            wants.extend(oracle.brute_force_coreness(n, edges))
+    u = gg.disjoint_union(parts)
+    got, _ = run(pico, u, algo)
+    assert_same(got, np.array(wants, dtype=np.int32), f"union of small graphs ({algo})")
+
+
+CLOSED = [
+    ("K2", lambda: gg.complete_graph(2), 1),
+    ("K64", lambda: gg.complete_graph(64), 63),
+    ("K2100", lambda: gg.complete_graph(2100), 2099),   # HistoCore CTA walk (K > 2048)
+    ("C1000", lambda: gg.cycle_graph(1000), 2),
+    ("P5000", lambda: gg.path_graph(5000), 1),           # ~2500 frontier waves
+    ("star70000", lambda: gg.star_graph(70000), 1),      # hub split into 69 chunks
+    ("grid300x200", lambda: gg.grid_graph(300, 200), 2),
+    ("K40,3000", lambda: gg.complete_bipartite(40, 3000), 40),
+    ("Q10", lambda: gg.hypercube(10), 10),
+    ("tree20000", lambda: gg.random_tree(20000, 3), 1),
+]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("name,make,k", CLOSED, ids=[c[0] for c in CLOSED])
+def test_closed_forms(pico, algo, name, make, k):
+    g = make()
+    got, _ = run(pico, g, algo)
+    assert (got == k).all(), f"{name}: values {np.unique(got)[:10]}"
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_isolated_and_empty(pico, algo):
+    g = gg.from_edge_list([], 1000)
+    got, _ = run(pico, g, algo)
+    assert (got == 0).all()
+    g = gg.from_edge_list([(3, 7)], 10)
+    got, _ = run(pico, g, algo)
+    assert got.tolist() == [0, 0, 0, 1, 0, 0, 0, 1, 0, 0]
+    import paper_2402_15253_gb300 as p
+    rp = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = p.coreness(rp, torch.zeros(0, dtype=torch.int32, device="cuda"), algo)
+    assert out.numel() == 0
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_random_small_graphs(pico, algo):
+    rng = np.random.default_rng(5)
+    parts, wants = [], []
+    for t in range(200):
+        n = int(rng.integers(2, 65))
+        p = [0.03, 0.08, 0.15, 0.3, 0.6][t % 5]
+        edges = [(u, v) for u in range(n) for v in range(u + 1, n) if rng.random() < p]
+        parts.append(gg.from_edge_list(edges, n))
+        wants.extend(oracle.brute_force_coreness(n, edges))
+    got, _ = run(pico, gg.disjoint_union(parts), algo)
+    assert_same(got, np.array(wants, dtype=np.int32), "random small graphs")
+
+
+# --------------------------------------------------------------------------
+# synthetic families, several tiles and ragged tails, against BZ and the
+# iteration structure of the sequential renditions
+# --------------------------------------------------------------------------
+
+FAMILIES = [
+    ("rmat16", lambda: gg.workload("rmat16")),
+    ("rmat14-ef8", lambda: gg.rmat_graph(14, 8, 31)),
+    ("er-50k", lambda: gg.er_graph(50001, 400003, 32)),
+    ("chunglu-2^16", lambda: gg.chung_lu_graph(1 << 16, 33, clique=300)),
+    ("grid-257x333", lambda: gg.grid_graph(257, 333)),
+]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("name,make", FAMILIES, ids=[f[0] for f in FAMILIES])
+def test_families_match_oracle(pico, algo, name, make):
+    g = make()
+    rp, ci = g.numpy()
+    want = oracle.bz_coreness(rp, ci)
+    got, st = run(pico, g, algo)
+    assert_same(got, want, f"{name} {algo}")
+    if algo == "peelone":
+        _, ost = oracle.peelone(rp, ci)
+        assert st["levels"] == ost["levels"]
+        assert st["kmax"] == ost["kmax"]
+        assert st["subrounds"] == ost["waves"]
+        assert st["arcs"] == ost["arcs_scanned"]
+    else:
+        _, ost = oracle.histocore(rp, ci)
+        assert st["rounds"] == ost["rounds"]
+        assert st["frontier"] == ost["frontier"]
+        assert st["slots"] == ost["slots_read"]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_int64_offsets(pico, algo):
+    g = gg.rmat_graph(15, 16, 34)
+    want = oracle.bz_coreness(*g.numpy())
+    got, _ = run(pico, g, algo, off_dtype=torch.int64)
+    assert_same(got, want, "int64 row_ptr")
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_side_stream_and_repeat(pico, algo):
+    g = gg.rmat_graph(14, 16, 35)
+    want = oracle.bz_coreness(*g.numpy())
+    rp, ci = g.row_ptr.cuda(), g.col_idx.cuda()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        outs = [pico.coreness(rp, ci, algo, check=False) for _ in range(3)]
+    assert pico.pico_last_device_status(s) == 0
+    for o in outs:
+        assert_same(o.cpu().numpy(), want, "side stream")
+
+
+# --------------------------------------------------------------------------
+# full-size workloads (the launch configuration the benchmark times)
+# --------------------------------------------------------------------------
+
+FULL = ["rmat22", "rmat24", "chunglu24", "grid4096"]
+
+
+@pytest.mark.parametrize("name", FULL)
+def test_full_size_workloads(pico, name):
+    g = gg.workload(name, device="cuda")
+    rp, ci = g.numpy()
+    want = oracle.bz_coreness(rp, ci)
+    for algo in ALGOS:
+        out = pico.coreness(g.row_ptr, g.col_idx, algo)
+        assert_same(out.cpu().numpy(), want, f"{name} {algo}")
+    if name == "chunglu24":
+        members = gg.clique_members(g.n, gg.SEED_BASE + 3, 3000).numpy()
+        assert (want[members] >= 2999).all()
+    if name == "grid4096":
+        assert (want == 2).all()
