@@ -27,7 +27,6 @@ import re
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -76,18 +75,28 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, method: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (its `kernel_source_hash` line matches)."""
-    path = os.path.join(ROOT, "profiles", f"{method}_{workload}.md")
-    if not os.path.exists(path):
-        return None
-    text = open(path).read()
-    m1 = re.search(r"kernel_source_hash\s*=\s*`?([0-9a-f]+)", text)
-    m2 = re.search(r"dram_bytes_per_launch\s*=\s*`?([0-9.eE+]+)", text)
-    if not (m1 and m2) or m1.group(1) != kernel_source_hash():
-        return None
-    return float(m2.group(1))
+def recorded_traffic(workload: str, method: str, arcs: int):
+    """DRAM bytes per launch from a committed ncu summary of `method`, if it
+    was taken on the current kernel sources (its `kernel_source_hash` line
+    matches). A capture of a smaller workload of the same family is scaled to
+    this one by the arc count (the traffic of both methods grows with the
+    arcs they scan). Returns (bytes or None, source description)."""
+    best = None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{method}_*.md"))):
+        text = open(path).read()
+        m_hash = re.search(r"kernel_source_hash\s*=\s*`?([0-9a-f]+)", text)
+        m_bytes = re.search(r"dram_bytes_per_launch\s*=\s*`?([0-9.eE+]+)", text)
+        m_wl = re.search(r"workload\s*=\s*(\w+)", text)
+        m_arcs = re.search(r"arcs\s*=\s*([0-9]+)", text)
+        if not (m_hash and m_bytes and m_wl and m_arcs) or m_hash.group(1) != kernel_source_hash():
+            continue
+        wl = m_wl.group(1)
+        if wl == workload:
+            return float(m_bytes.group(1)), f"ncu capture of {wl}"
+        if wl.rstrip("0123456789") == workload.rstrip("0123456789"):
+            best = (float(m_bytes.group(1)) * arcs / int(m_arcs.group(1)),
+                    f"ncu capture of {wl}, scaled by arcs")
+    return best if best else (None, "no capture of the current kernel sources")
 
 
 class ClockSampler:
@@ -308,7 +317,7 @@ def main():
     mean_ms = {a: statistics.mean(v) for a, v in per.items()}
     dom = max(mean_ms, key=mean_ms.get)
     achieved = b_min / (mean_ms[dom] / 1000.0) / 1e9
-    traffic = recorded_traffic(args.workload, dom)
+    traffic, traffic_src = recorded_traffic(args.workload, dom, arcs)
     methods = {a: {"ms_mean": mean_ms[a], "ms_median": statistics.median(per[a]),
                    "edges_per_s": m_und / (mean_ms[a] / 1000.0),
                    "bmin_gbs": b_min / (mean_ms[a] / 1000.0) / 1e9,
@@ -328,6 +337,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": traffic_src,
                      "bytes_per_launch": b_min, "peak_kind": peak_kind,
                      "bytes_model": "B_min = w_r(n+1) + 8 B/arc + 4 B/vertex"},
         "methods": methods,

@@ -109,7 +109,12 @@ typedef struct {
     int64_t atomics;     /* atomic read-modify-writes on core[] or histo[] */
     int64_t slots;       /* HistoCore: histogram slots read by SumHisto */
     int64_t blocks;      /* CTAs of the persistent launch */
-    int64_t reserved[4];
+    /* Device time (ns) and count per phase kind, measured by CTA 0 from one
+       grid barrier to the next: [0] init, [1] PeelOne residual scan,
+       [2..4] PeelOne frontier waves with < 64 work units / fewer units than
+       warps / more, [5] InitHisto, [6] SumHisto, [7] UpdateHisto. */
+    int64_t phase_ns[8];
+    int64_t phase_count[8];
 } pico_stats;
 
 int pico_get_stats(pico_stream_t stream, pico_stats *out);

@@ -41,13 +41,21 @@ class PicoError(RuntimeError):
                          else f"{pico_status_string(status)} ({status})")
 
 
+PHASES = ("init", "scan", "wave_tiny", "wave_mid", "wave_wide", "inithisto", "sumhisto",
+          "updatehisto")
+
+
 class pico_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "algo", "levels", "kmax", "subrounds", "scans", "rounds", "frontier", "barriers",
-        "arcs", "atomics", "slots", "blocks")] + [("reserved", ctypes.c_int64 * 4)]
+        "arcs", "atomics", "slots", "blocks")] + [("phase_ns", ctypes.c_int64 * 8),
+                                                  ("phase_count", ctypes.c_int64 * 8)]
 
     def as_dict(self) -> dict:
-        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+        d = {f: int(getattr(self, f)) for f, _ in self._fields_ if not f.startswith("phase")}
+        d["phases"] = {PHASES[i]: {"ms": self.phase_ns[i] / 1e6, "count": int(self.phase_count[i])}
+                       for i in range(8) if self.phase_count[i]}
+        return d
 
 
 _lib = None

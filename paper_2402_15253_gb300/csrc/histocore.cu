@@ -64,15 +64,21 @@ template <typename Off>
 struct InitArc {
     const int *core;
     int *histo;
-    unsigned long long arcs = 0;
+    unsigned long long n_arcs = 0;
     __device__ __forceinline__ void item(int v, int &a, int &) { a = ldcg(core + v); }
-    __device__ __forceinline__ void arc(bool valid, int, int u, Off, Off rs, int dv, int)
+    __device__ __forceinline__ void arcs(const bool (&valid)[kU], const int (&)[kU],
+                                         const int (&u)[kU], const Off (&rs)[kU],
+                                         const int (&dv)[kU], const int (&)[kU])
     {
-        if (valid) {
-            ++arcs;
-            const int du = ldcg(core + u);
-            atomicAdd(histo + rs + (du < dv ? du : dv) - 1, 1);
-        }
+        int du[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) du[j] = valid[j] ? ldcg(core + u[j]) : 0;
+#pragma unroll
+        for (int j = 0; j < kU; ++j)
+            if (valid[j]) {
+                ++n_arcs;
+                atomicAdd(histo + rs[j] + (du[j] < dv[j] ? du[j] : dv[j]) - 1, 1);
+            }
     }
 };
 
@@ -84,42 +90,57 @@ struct UpdateArc {
     int *histo;
     int *tl, *wl, *bl;
     Ctrl *ctl;
-    int par;   // parity of the next round's lists
+    int par;        // parity of the next round's lists
     unsigned cap;   // slots of each list (n)
-    unsigned long long arcs = 0, atomics = 0;
+    unsigned long long n_arcs = 0, n_atomics = 0;
 
     __device__ __forceinline__ void item(int v, int &x, int &y)
     {
         x = ldcg(oldcore + v);
         y = ldcg(core + v);
     }
-    __device__ __forceinline__ void arc(bool valid, int, int u, Off, Off, int x, int y)
+    __device__ __forceinline__ void arcs(const bool (&valid)[kU], const int (&)[kU],
+                                         const int (&u)[kU], const Off (&)[kU],
+                                         const int (&x)[kU], const int (&y)[kU])
     {
-        bool push = false;
-        int K = 0;
-        if (valid) {
-            ++arcs;
-            K = ldcg(core + u);
-            if (K > y) {
-                const Off ru = rp[u];
-                const int sa = x < K ? x : K;
-                const int old = atomicSub(histo + ru + sa - 1, 1);
-                atomicAdd(histo + ru + y - 1, 1);
-                atomics += 2;
-                push = (x >= K) && (old == K);
+        int K[kU], old[kU];
+        Off ru[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            K[j] = valid[j] ? ldcg(core + u[j]) : 0;
+            ru[j] = valid[j] ? rp[u[j]] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            old[j] = 0;
+            if (valid[j]) {
+                ++n_arcs;
+                if (K[j] > y[j]) {   // types N1 and N3: the change is visible to u
+                    if (x[j] >= K[j]) {   // slot K holds cnt: its old value decides the append
+                        old[j] = atomicSub(histo + ru[j] + K[j] - 1, 1);
+                    } else {              // slot x < K: no append can follow
+                        atomicSub(histo + ru[j] + x[j] - 1, 1);
+                    }
+                    atomicAdd(histo + ru[j] + y[j] - 1, 1);
+                    n_atomics += 2;
+                }
             }
         }
-        const int cls = kclass(K);
         unsigned *live = ctl->live.w + 3 * par;
-        const unsigned p0 = warp_push(&live[L_T], push && cls == 0);
-        const unsigned p1 = warp_push(&live[L_W], push && cls == 1);
-        const unsigned p2 = warp_push(&live[L_B], push && cls == 2);
-        if (push) {
-            const unsigned pos = cls == 0 ? p0 : (cls == 1 ? p1 : p2);
-            if (pos >= cap) set_error(ctl, kErrNotConverged);
-            else if (cls == 0) tl[pos] = u;
-            else if (cls == 1) wl[pos] = u;
-            else bl[pos] = u;
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            const bool push = valid[j] && K[j] > y[j] && x[j] >= K[j] && old[j] == K[j];
+            const int cls = kclass(K[j]);
+            const unsigned p0 = warp_push(&live[L_T], push && cls == 0);
+            const unsigned p1 = warp_push(&live[L_W], push && cls == 1);
+            const unsigned p2 = warp_push(&live[L_B], push && cls == 2);
+            if (push) {
+                const unsigned pos = cls == 0 ? p0 : (cls == 1 ? p1 : p2);
+                if (pos >= cap) set_error(ctl, kErrNotConverged);
+                else if (cls == 0) tl[pos] = u[j];
+                else if (cls == 1) wl[pos] = u[j];
+                else bl[pos] = u[j];
+            }
         }
     }
 };
@@ -261,7 +282,7 @@ __device__ __forceinline__ long long sum_thread(const HistoParams<Off> &p, int v
 }
 
 template <typename Off>
-__global__ void __launch_bounds__(kThreads) histocore_kernel(HistoParams<Off> p)
+__global__ void __launch_bounds__(kThreads, 2) histocore_kernel(HistoParams<Off> p)
 {
     __shared__ unsigned s_snap[kLiveWords + 1];
     __shared__ unsigned s_tmp[256];
@@ -273,8 +294,12 @@ __global__ void __launch_bounds__(kThreads) histocore_kernel(HistoParams<Off> p)
     const unsigned nthreads = gridDim.x * blockDim.x;
     const unsigned gwarp = tid >> 5, nwarps = nthreads >> 5;
     const long long n = p.n;
-    unsigned long long st[kStCount] = {};
+    __shared__ unsigned long long st[kStCount];   // uniform statistics, thread 0 only
+    if (threadIdx.x < kStCount) st[threadIdx.x] = 0;
+    __syncthreads();
     unsigned long long arcs = 0, atomics = 0, slots = 0;
+    PhaseClock clk;
+    clk.start();
 
     // core = degree; chunk list of the large vertices for InitHisto
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += nthreads) {
@@ -292,18 +317,20 @@ __global__ void __launch_bounds__(kThreads) histocore_kernel(HistoParams<Off> p)
             set_error(ctl, kErrNotConverged);
     }
     if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-    ++st[kStBarriers];
+    if (threadIdx.x == 0) ++st[kStBarriers];
+    clk.end(st, kPhInit);
 
     // InitHisto
     {
         InitArc<Off> f{p.core, p.histo};
         expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, p.ub, s_snap[L_IB], gwarp, nwarps,
                f);
-        arcs += f.arcs;
-        atomics += f.arcs;
+        arcs += f.n_arcs;
+        atomics += f.n_arcs;
     }
     if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-    ++st[kStBarriers];
+    if (threadIdx.x == 0) ++st[kStBarriers];
+    clk.end(st, kPhInitHisto);
 
     // initial V_cnt (parity 0)
     for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += nthreads) {
@@ -321,7 +348,8 @@ __global__ void __launch_bounds__(kThreads) histocore_kernel(HistoParams<Off> p)
         if (in[2]) p.bl[0][pos[2]] = (int)v;
     }
     if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-    ++st[kStBarriers];
+    if (threadIdx.x == 0) ++st[kStBarriers];
+    clk.end(st, kPhInit);
 
     {
         const long long max_rounds = p.m + 2;
@@ -334,8 +362,8 @@ __global__ void __launch_bounds__(kThreads) histocore_kernel(HistoParams<Off> p)
                 if (threadIdx.x == 0) set_error(ctl, kErrNotConverged);
                 break;
             }
-            ++st[kStRounds];
-            st[kStFrontier] += nt + nwl + nb;
+            if (threadIdx.x == 0) ++st[kStRounds];
+            if (threadIdx.x == 0) st[kStFrontier] += nt + nwl + nb;
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 const int np = 1 - par;
                 live[3 * np + L_T] = 0;
@@ -364,7 +392,8 @@ __global__ void __launch_bounds__(kThreads) histocore_kernel(HistoParams<Off> p)
                 if (d > kSmallDeg) list_changed(p, v, d);
             }
             if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-            ++st[kStBarriers];
+            if (threadIdx.x == 0) ++st[kStBarriers];
+            clk.end(st, kPhSumHisto);
 
             // UpdateHisto over the changed vertices
             const unsigned nus = s_snap[L_US], nub = s_snap[L_UB];
@@ -377,19 +406,19 @@ __global__ void __launch_bounds__(kThreads) histocore_kernel(HistoParams<Off> p)
                 UpdateArc<Off> f{p.rp, p.core, p.oldcore, p.histo, p.tl[np], p.wl[np], p.bl[np],
                                  ctl, np, (unsigned)n};
                 expand(p.rp, p.ci, p.us, nus, p.ub, nub, gwarp, nwarps, f);
-                arcs += f.arcs;
-                atomics += f.atomics;
+                arcs += f.n_arcs;
+                atomics += f.n_atomics;
             }
             if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-            ++st[kStBarriers];
+            if (threadIdx.x == 0) ++st[kStBarriers];
+            clk.end(st, kPhUpdateHisto);
         }
     }
 done:
     block_sum_to(arcs, &ctl->stats[kStArcs], s_red);
     block_sum_to(atomics, &ctl->stats[kStAtomics], s_red);
     block_sum_to(slots, &ctl->stats[kStSlots], s_red);
-    if (blockIdx.x != 0)
-        for (int i = 0; i < kStCount; ++i) st[i] = 0;
+    if (blockIdx.x != 0 && threadIdx.x < kStCount) st[threadIdx.x] = 0;
     finish_block(ctl, p.last, 1, st, kStCount);
 }
 

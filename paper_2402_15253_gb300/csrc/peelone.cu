@@ -31,6 +31,8 @@ namespace {
 
 enum : int { L_QS = 0, L_QB = 1, L_KEPT = 2 /* 2..4 */, L_MIN = 5 /* 5..7 */ };
 
+constexpr int kScanItems = 4;   // residual-list entries per thread per scan step
+
 template <typename Off>
 struct PeelParams {
     const Off *rp;
@@ -56,36 +58,46 @@ struct PeelArc {
     Ctrl *ctl;
     int k;
     unsigned qs_cap;
-    unsigned long long arcs = 0, atomics = 0;
+    unsigned long long n_arcs = 0, n_atomics = 0;
 
     __device__ __forceinline__ void item(int, int &, int &) {}
 
-    __device__ __forceinline__ void arc(bool valid, int, int u, Off, Off, int, int)
+    __device__ __forceinline__ void arcs(const bool (&valid)[kU], const int (&)[kU],
+                                         const int (&u)[kU], const Off (&)[kU],
+                                         const int (&)[kU], const int (&)[kU])
     {
-        bool push = false;
-        if (valid) {
-            ++arcs;
-            const int c = ldcg(core + u);
-            if (c > k) {
-                const int old = atomicSub(core + u, 1);
-                ++atomics;
-                push = (old == k + 1);
+        int c[kU], old[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) c[j] = valid[j] ? ldcg(core + u[j]) : 0;
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            old[j] = 0;
+            if (valid[j]) {
+                ++n_arcs;
+                if (c[j] > k) {
+                    old[j] = atomicSub(core + u[j], 1);
+                    ++n_atomics;
+                }
             }
         }
-        long long d = 0;
-        bool small = false, large = false;
-        if (push) {
-            d = (long long)(rp[u + 1] - rp[u]);
-            small = d <= kSmallDeg;
-            large = !small;
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            // the decrement that moved u from k + 1 to k appends it (once)
+            const bool push = valid[j] && c[j] > k && old[j] == k + 1;
+            long long d = 0;
+            bool small = false, large = false;
+            if (push) {
+                d = (long long)(rp[u[j] + 1] - rp[u[j]]);
+                small = d <= kSmallDeg;
+                large = !small;
+            }
+            const unsigned pos = warp_push(&ctl->live.w[L_QS], small);
+            if (small) {
+                if (pos < qs_cap) qs[pos] = u[j];
+                else set_error(ctl, kErrNotConverged);
+            }
+            warp_push_chunks(large, u[j], d, qb, &ctl->live.w[L_QB], qb_cap, ctl);
         }
-        const unsigned pos = warp_push(&ctl->live.w[L_QS], small);
-        if (small) {
-            if (pos < qs_cap) qs[pos] = u;
-            else set_error(ctl, kErrNotConverged);
-        }
-        if (large && !push_chunks(u, d, qb, &ctl->live.w[L_QB], qb_cap))
-            set_error(ctl, kErrNotConverged);
     }
 };
 
@@ -98,7 +110,7 @@ __device__ __forceinline__ void repair(const PeelParams<Off> &p, int k, unsigned
 }
 
 template <typename Off>
-__global__ void __launch_bounds__(kThreads) peelone_kernel(PeelParams<Off> p)
+__global__ void __launch_bounds__(kThreads, 2) peelone_kernel(PeelParams<Off> p)
 {
     __shared__ unsigned s_snap[kLiveWords + 1];
     __shared__ unsigned s_tmp[128];
@@ -110,8 +122,12 @@ __global__ void __launch_bounds__(kThreads) peelone_kernel(PeelParams<Off> p)
     const unsigned nthreads = gridDim.x * blockDim.x;
     const unsigned gwarp = tid >> 5, nwarps = nthreads >> 5;
     const long long n = p.n;
-    unsigned long long st[kStCount] = {};
+    __shared__ unsigned long long st[kStCount];   // uniform statistics, thread 0 only
+    if (threadIdx.x < kStCount) st[threadIdx.x] = 0;
+    __syncthreads();
     unsigned long long arcs = 0, atomics = 0;
+    PhaseClock clk;
+    clk.start();
 
     // init: core = degree; residual list = non-isolated vertices
     {
@@ -132,7 +148,8 @@ __global__ void __launch_bounds__(kThreads) peelone_kernel(PeelParams<Off> p)
         block_max_to(mx, &live[L_MIN], s_tmp);
     }
     if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-    ++st[kStBarriers];
+    if (threadIdx.x == 0) ++st[kStBarriers];
+    clk.end(st, kPhInit);
     {
         unsigned nres = s_snap[L_KEPT];
         int k = INT_MAX - (int)s_snap[L_MIN];
@@ -156,41 +173,52 @@ __global__ void __launch_bounds__(kThreads) peelone_kernel(PeelParams<Off> p)
             if (prev_k >= 0) repair(p, prev_k, r_s0, r_e0, r_s1, r_e1, tid, nthreads);
             prev_k = -1;
 
-            // scan the residual list at level k
+            // scan the residual list at level k (kScanItems vertices per thread)
             const int *rin = cur ? p.res1 : p.res0;
             int *rout = cur ? p.res0 : p.res1;
             unsigned mx = 0;
-            for (long long base = (long long)blockIdx.x * blockDim.x; base < nres;
-                 base += nthreads) {
-                const long long i = base + threadIdx.x;
-                bool fr_small = false, fr_large = false, keep = false;
-                int v = 0, c = 0;
-                long long d = 0;
-                if (i < nres) {
-                    v = ldcg(rin + i);
-                    c = ldcg(p.core + v);
-                    keep = c > k;
-                    if (c == k) {
-                        d = (long long)(p.rp[v + 1] - p.rp[v]);
-                        fr_small = d <= kSmallDeg;
-                        fr_large = !fr_small;
-                    }
-                    if (keep) mx = max(mx, (unsigned)(INT_MAX - c));
+            const long long step = (long long)nthreads * kScanItems;
+            for (long long base = (long long)blockIdx.x * blockDim.x * kScanItems; base < nres;
+                 base += step) {
+                int v[kScanItems], c[kScanItems];
+                long long d[kScanItems];
+#pragma unroll
+                for (int j = 0; j < kScanItems; ++j) {
+                    const long long i = base + threadIdx.x + (long long)j * blockDim.x;
+                    v[j] = i < nres ? ldcg(rin + i) : -1;
+                }
+#pragma unroll
+                for (int j = 0; j < kScanItems; ++j) c[j] = v[j] >= 0 ? ldcg(p.core + v[j]) : -1;
+                unsigned nsmall = 0, nkeep = 0;
+#pragma unroll
+                for (int j = 0; j < kScanItems; ++j) {
+                    d[j] = 0;
+                    if (c[j] == k) d[j] = (long long)(p.rp[v[j] + 1] - p.rp[v[j]]);
+                    nsmall += (c[j] == k && d[j] <= kSmallDeg);
+                    nkeep += (c[j] > k);
+                    if (c[j] > k) mx = max(mx, (unsigned)(INT_MAX - c[j]));
                 }
                 unsigned pq, pk;
-                block_push2(fr_small, keep, &live[L_QS], &live[L_KEPT + slot], pq, pk, s_tmp);
-                if (fr_small) {
-                    if (pq < (unsigned)n) p.qs[pq] = v;
-                    else set_error(ctl, kErrNotConverged);
+                block_alloc2(nsmall, nkeep, &live[L_QS], &live[L_KEPT + slot], pq, pk, s_tmp);
+#pragma unroll
+                for (int j = 0; j < kScanItems; ++j) {
+                    if (c[j] == k && d[j] <= kSmallDeg) {
+                        if (pq < (unsigned)n) p.qs[pq] = v[j];
+                        else set_error(ctl, kErrNotConverged);
+                        ++pq;
+                    }
+                    if (c[j] > k) rout[pk++] = v[j];   // pk < nres <= n
                 }
-                if (keep) rout[pk] = v;   // pk < nres <= n
-                if (fr_large && !push_chunks(v, d, p.qb, &live[L_QB], p.qb_cap))
-                    set_error(ctl, kErrNotConverged);
+#pragma unroll
+                for (int j = 0; j < kScanItems; ++j)
+                    warp_push_chunks(c[j] == k && d[j] > kSmallDeg, v[j], d[j], p.qb, &live[L_QB],
+                                     p.qb_cap, ctl);
             }
             block_max_to(mx, &live[L_MIN + slot], s_tmp);
             if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-            ++st[kStBarriers];
-            ++st[kStScans];
+            if (threadIdx.x == 0) ++st[kStBarriers];
+            if (threadIdx.x == 0) ++st[kStScans];
+            clk.end(st, kPhScan);
 
             const unsigned qs0 = qs_tail, qb0 = qb_tail;
             unsigned e0 = s_snap[L_QS], e1 = s_snap[L_QB];
@@ -202,19 +230,21 @@ __global__ void __launch_bounds__(kThreads) peelone_kernel(PeelParams<Off> p)
                 k = kmin_kept;
                 continue;
             }
-            ++st[kStLevels];
-            st[kStKmax] = (unsigned long long)k;
+            if (threadIdx.x == 0) ++st[kStLevels];
+            if (threadIdx.x == 0) st[kStKmax] = (unsigned long long)k;
 
             // scatter, wave by wave (dynamic frontier)
             unsigned s0 = qs0, s1 = qb0;
             while (s0 < e0 || s1 < e1) {
+                const unsigned units = (e0 - s0 + 31) / 32 + (e1 - s1);
                 PeelArc<Off> f{p.rp, p.core, p.qs, p.qb, p.qb_cap, ctl, k, (unsigned)n};
                 expand(p.rp, p.ci, p.qs + s0, e0 - s0, p.qb + s1, e1 - s1, gwarp, nwarps, f);
-                arcs += f.arcs;
-                atomics += f.atomics;
+                arcs += f.n_arcs;
+                atomics += f.n_atomics;
                 if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-                ++st[kStBarriers];
-                ++st[kStSubrounds];
+                if (threadIdx.x == 0) ++st[kStBarriers];
+                if (threadIdx.x == 0) ++st[kStSubrounds];
+                clk.end(st, units < 64 ? kPhWaveTiny : (units < nwarps ? kPhWaveMid : kPhWaveWide));
                 s0 = e0;
                 s1 = e1;
                 e0 = s_snap[L_QS];
@@ -231,8 +261,7 @@ __global__ void __launch_bounds__(kThreads) peelone_kernel(PeelParams<Off> p)
 done:
     block_sum_to(arcs, &ctl->stats[kStArcs], s_red);
     block_sum_to(atomics, &ctl->stats[kStAtomics], s_red);
-    if (blockIdx.x != 0)
-        for (int i = 0; i < kStCount; ++i) st[i] = 0;
+    if (blockIdx.x != 0 && threadIdx.x < kStCount) st[threadIdx.x] = 0;
     finish_block(ctl, p.last, 0, st, kStCount);
 }
 

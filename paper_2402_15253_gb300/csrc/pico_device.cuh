@@ -24,7 +24,7 @@ namespace pico {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSmallDeg = 32;     // degree at or below which a vertex is "small"
-constexpr int kChunk = 1024;      // arcs per chunk of a large vertex
+constexpr int kChunk = 256;       // arcs per chunk of a large vertex
 constexpr int kThreads = 512;     // threads per CTA of the persistent kernels
 constexpr int kLiveWords = 32;
 
@@ -42,8 +42,18 @@ struct alignas(128) Line {
 // Statistics slots (match pico_stats field order after `algo`).
 enum StatIdx : int {
     kStLevels = 0, kStKmax, kStSubrounds, kStScans, kStRounds, kStFrontier,
-    kStBarriers, kStArcs, kStAtomics, kStSlots, kStBlocks, kStCount = 16
+    kStBarriers, kStArcs, kStAtomics, kStSlots, kStBlocks,
+    kStPhaseNs = 16,      // 16..23: device time per phase kind (CTA 0's view)
+    kStPhaseCount = 24,   // 24..31: phases per kind
+    kStCount = 32
 };
+
+// Phase kinds for the timing statistics.
+enum PhaseKind : int {
+    kPhInit = 0, kPhScan, kPhWaveTiny, kPhWaveMid, kPhWaveWide, kPhInitHisto, kPhSumHisto,
+    kPhUpdateHisto
+};
+
 
 struct Ctrl {
     Line bar;                 // w[0] arrivals, w[1] generation
@@ -71,6 +81,24 @@ __device__ __forceinline__ unsigned long long gtime()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// Per-phase device time, kept by thread 0 of CTA 0 (the only writer).
+struct PhaseClock {
+    unsigned long long t_prev = 0;
+    __device__ __forceinline__ void start()
+    {
+        if (blockIdx.x == 0 && threadIdx.x == 0) t_prev = gtime();
+    }
+    __device__ __forceinline__ void end(unsigned long long *st, int kind)
+    {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const unsigned long long t = gtime();
+            st[kStPhaseNs + kind] += t - t_prev;
+            st[kStPhaseCount + kind] += 1;
+            t_prev = t;
+        }
+    }
+};
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
@@ -116,22 +144,35 @@ __device__ __forceinline__ int status_of(Ctrl *c)
 // ---------------------------------------------------------------------------
 // s_snap: shared memory, kLiveWords + 1 words; after the call s_snap[i] holds
 // the live counter i as of the barrier and s_snap[kLiveWords] the status.
+// Warp 0 of each CTA takes part: lane 0 arrives and waits, and the snapshot
+// is copied and read with one word per lane (a single memory round trip).
 static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap, unsigned long long limit_ns)
 {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned nblocks = gridDim.x;
-        unsigned gen = ld_acquire(&c->bar.w[1]);
-        __threadfence();
-        unsigned prev = atomicAdd(&c->bar.w[0], 1u);
-        if (prev == nblocks - 1) {
+    if (threadIdx.x < 32) {
+        const unsigned lane = threadIdx.x;
+        unsigned gen = 0, prev = 0;
+        if (lane == 0) {
+            gen = ld_acquire(&c->bar.w[1]);
             __threadfence();
-            unsigned *dst = c->snap[(gen + 1) & 1].w;
-            for (int i = 0; i < kLiveWords; ++i) dst[i] = ld_relaxed(&c->live.w[i]);
-            atomicExch(&c->bar.w[0], 0u);
+            prev = atomicAdd(&c->bar.w[0], 1u);
+        }
+        gen = __shfl_sync(kFull, gen, 0);
+        prev = __shfl_sync(kFull, prev, 0);
+        const unsigned par = (gen + 1) & 1;
+        if (prev == gridDim.x - 1) {
+            // last arrival: every lane synchronises with the other CTAs'
+            // arrivals before reading the counters they updated
+            (void)ld_acquire(&c->bar.w[0]);
+            c->snap[par].w[lane] = ld_relaxed(&c->live.w[lane]);
             __threadfence();
-            st_release(&c->bar.w[1], gen + 1);
-        } else {
+            __syncwarp();
+            if (lane == 0) {
+                atomicExch(&c->bar.w[0], 0u);
+                __threadfence();
+                st_release(&c->bar.w[1], gen + 1);
+            }
+        } else if (lane == 0) {
             const unsigned long long t0 = gtime();
             unsigned spins = 0;
             while (ld_acquire(&c->bar.w[1]) == gen) {
@@ -144,10 +185,10 @@ static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap, unsigne
                 }
             }
         }
-        __threadfence();
-        const unsigned *src = c->snap[(gen + 1) & 1].w;
-        for (int i = 0; i < kLiveWords; ++i) s_snap[i] = ld_relaxed(src + i);
-        s_snap[kLiveWords] = (unsigned)status_of(c);
+        __syncwarp();
+        (void)ld_acquire(&c->bar.w[1]);   // every lane acquires the release
+        s_snap[lane] = ld_relaxed(c->snap[par].w + lane);
+        if (lane == 0) s_snap[kLiveWords] = (unsigned)status_of(c);
     }
     __syncthreads();
     return s_snap[kLiveWords] == 0;
@@ -268,11 +309,41 @@ __device__ __forceinline__ bool push_chunks(int v, long long d, int2 *list, unsi
     return true;
 }
 
+// Warp-cooperative append of the chunk entries of large vertices: every
+// lane with `pred` owns vertex v of degree d; the whole warp writes the
+// ceil(d / kChunk) entries of each such vertex in turn.
+__device__ __forceinline__ void warp_push_chunks(bool pred, int v, long long d, int2 *list,
+                                                 unsigned *counter, unsigned cap, Ctrl *ctl)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned m = __ballot_sync(kFull, pred);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int vv = __shfl_sync(kFull, v, src);
+        const long long dd = __shfl_sync(kFull, d, src);
+        const unsigned nch = (unsigned)((dd + kChunk - 1) / kChunk);
+        unsigned pos = 0;
+        if (lane == 0) pos = atomicAdd(counter, nch);
+        pos = __shfl_sync(kFull, pos, 0);
+        if ((unsigned long long)pos + nch > cap) {
+            if (lane == 0) set_error(ctl, kErrNotConverged);
+            continue;
+        }
+        for (unsigned c = lane; c < nch; c += 32) list[pos + c] = make_int2(vv, (int)c);
+    }
+}
+
+// Arcs issued per lane per step of expand(): their loads and atomics are
+// independent, so up to kU memory round trips per lane are in flight.
+constexpr int kU = 4;
+
 // Functor interface used by expand():
 //   void item(int v, int &a, int &b)     per-vertex prologue (lane-local)
-//   void arc(bool valid, int v, int u, Off e, Off rs, int a, int b)
-//                                        called by ALL 32 lanes together;
-//                                        e is the arc index, rs = row_ptr[v]
+//   void arcs(const bool (&valid)[kU], const int (&v)[kU], const int (&u)[kU],
+//             const Off (&rs)[kU], const int (&a)[kU], const int (&b)[kU])
+//                                        called by ALL 32 lanes together with
+//                                        kU arcs (v -> u) per lane; rs = row_ptr[v]
 // `small` lists small vertices (nullptr: the identity list 0..nsmall-1, where
 // vertices with degree > kSmallDeg are skipped because their chunks are in
 // `big`). `big` lists (vertex, chunk) pairs.
@@ -306,23 +377,28 @@ __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__
             }
             const int excl = incl - d;
             const int T = __shfl_sync(kFull, incl, 31);
-            for (int base = 0; base < T; base += 32) {
-                const int fidx = base + lane;
-                int o = 0;
+            for (int base = 0; base < T; base += 32 * kU) {
+                bool valid[kU];
+                int vo[kU], u[kU], ao[kU], bo[kU];
+                Off rso[kU];
 #pragma unroll
-                for (int s = 16; s > 0; s >>= 1) {
-                    const int ex = __shfl_sync(kFull, excl, o + s);
-                    if (ex <= fidx) o += s;
+                for (int j = 0; j < kU; ++j) {
+                    const int fidx = base + 32 * j + lane;
+                    int o = 0;
+#pragma unroll
+                    for (int s = 16; s > 0; s >>= 1) {
+                        const int ex = __shfl_sync(kFull, excl, o + s);
+                        if (ex <= fidx) o += s;
+                    }
+                    vo[j] = __shfl_sync(kFull, v, o);
+                    rso[j] = __shfl_sync(kFull, rs, o);
+                    const int exo = __shfl_sync(kFull, excl, o);
+                    ao[j] = __shfl_sync(kFull, a, o);
+                    bo[j] = __shfl_sync(kFull, b, o);
+                    valid[j] = fidx < T;
+                    u[j] = valid[j] ? __ldg(ci + rso[j] + (fidx - exo)) : -1;
                 }
-                const int vo = __shfl_sync(kFull, v, o);
-                const Off rso = __shfl_sync(kFull, rs, o);
-                const int exo = __shfl_sync(kFull, excl, o);
-                const int ao = __shfl_sync(kFull, a, o);
-                const int bo = __shfl_sync(kFull, b, o);
-                const bool valid = fidx < T;
-                const Off e = rso + (fidx - exo);
-                const int u = valid ? __ldg(ci + e) : -1;
-                f.arc(valid, vo, u, e, rso, ao, bo);
+                f.arcs(valid, vo, u, rso, ao, bo);
             }
         } else {
             const int2 ent = __ldcg(big + (unit - nbatch));   // written by other CTAs
@@ -332,11 +408,21 @@ __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__
             const Off t = (s + kChunk < re) ? s + kChunk : re;
             int a = 0, b = 0;
             f.item(v, a, b);
-            for (Off e0 = s; e0 < t; e0 += 32) {
-                const Off e = e0 + lane;
-                const bool valid = e < t;
-                const int u = valid ? __ldg(ci + e) : -1;
-                f.arc(valid, v, u, e, rs, a, b);
+            for (Off e0 = s; e0 < t; e0 += 32 * kU) {
+                bool valid[kU];
+                int vo[kU], u[kU], ao[kU], bo[kU];
+                Off rso[kU];
+#pragma unroll
+                for (int j = 0; j < kU; ++j) {
+                    const Off e = e0 + 32 * j + lane;
+                    valid[j] = e < t;
+                    u[j] = valid[j] ? __ldg(ci + e) : -1;
+                    vo[j] = v;
+                    rso[j] = rs;
+                    ao[j] = a;
+                    bo[j] = b;
+                }
+                f.arcs(valid, vo, u, rso, ao, bo);
             }
         }
     }
@@ -451,6 +537,61 @@ __device__ __forceinline__ unsigned block_alloc(unsigned cnt, unsigned *counter,
     const unsigned r = s[32 + warp] + inc - cnt;
     __syncthreads();
     return r;
+}
+
+}  // namespace pico
+
+namespace pico {
+
+// Block-aggregated allocation from two counters at once: each thread asks
+// for n0 slots of *c0 and n1 slots of *c1 and receives its first slot of
+// each. Every thread of the CTA must call it. s: shared scratch >= 128 words.
+__device__ __forceinline__ void block_alloc2(unsigned n0, unsigned n1, unsigned *c0, unsigned *c1,
+                                             unsigned &b0, unsigned &b1, unsigned *s)
+{
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned i0 = n0, i1 = n1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y0 = __shfl_up_sync(kFull, i0, o), y1 = __shfl_up_sync(kFull, i1, o);
+        if ((int)lane >= o) {
+            i0 += y0;
+            i1 += y1;
+        }
+    }
+    if (lane == 31) {
+        s[warp] = i0;
+        s[32 + warp] = i1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned x0 = lane < nw ? s[lane] : 0u, x1 = lane < nw ? s[32 + lane] : 0u;
+        unsigned w0 = x0, w1 = x1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y0 = __shfl_up_sync(kFull, w0, o), y1 = __shfl_up_sync(kFull, w1, o);
+            if ((int)lane >= o) {
+                w0 += y0;
+                w1 += y1;
+            }
+        }
+        const unsigned t0 = __shfl_sync(kFull, w0, 31), t1 = __shfl_sync(kFull, w1, 31);
+        unsigned g0 = 0, g1 = 0;
+        if (lane == 0) {
+            if (t0) g0 = atomicAdd(c0, t0);
+            if (t1) g1 = atomicAdd(c1, t1);
+        }
+        g0 = __shfl_sync(kFull, g0, 0);
+        g1 = __shfl_sync(kFull, g1, 0);
+        if (lane < nw) {
+            s[64 + lane] = g0 + w0 - x0;
+            s[96 + lane] = g1 + w1 - x1;
+        }
+    }
+    __syncthreads();
+    b0 = s[64 + warp] + i0 - n0;
+    b1 = s[96 + warp] + i1 - n1;
+    __syncthreads();
 }
 
 }  // namespace pico
