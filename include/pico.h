@@ -80,6 +80,34 @@ int pico_coreness(const int32_t *row_ptr, const int32_t *col_idx, int64_t n, int
 int pico_coreness_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
                       int32_t *out_core, int algo, pico_stream_t stream);
 
+/*
+ * PeelOne for callers that cannot allocate device memory. The paper has no
+ * counterpart: this entry point exists for host code that must not call
+ * cudaMalloc or any other allocating routine while it runs, for example a
+ * service that reserved its whole device-memory budget at start-up, or an
+ * embedding framework that owns every allocation. It computes what
+ * pico_coreness(..., PICO_ALGO_PEELONE, ...) computes, allocates nothing, and
+ * takes its scratch from one array compiled into the library: 17 MiB of
+ * device memory that every GPU on which the library is loaded holds until
+ * the process exits.
+ *
+ * Limits: n <= PICO_NOALLOC_MAX_VERTICES and m <= PICO_NOALLOC_MAX_ARCS;
+ * larger graphs are rejected with PICO_ERR_INVALID_ARG before any GPU work.
+ * out_status: optional device int32 (NULL to skip) that receives the
+ * device-side status of this call (PICO_OK, or e.g. PICO_ERR_TIMEOUT) on
+ * `stream`; these calls do not update pico_last_device_status or
+ * pico_get_stats.
+ * The first call on a device looks up the array's device address (no
+ * allocation) and should come before any stream capture. All calls on a
+ * device share the array; each call clears what must start at zero, but
+ * calls whose GPU work overlaps (different streams, or threads racing) use
+ * the same memory at once and race: issue them one after another.
+ */
+#define PICO_NOALLOC_MAX_VERTICES (1 << 20)
+#define PICO_NOALLOC_MAX_ARCS (1 << 24)
+int pico_coreness_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                          int32_t *out_core, int32_t *out_status, pico_stream_t stream);
+
 /* Scratch bytes a single-graph call with these sizes allocates (admission
    accounting). Returns 0 for invalid arguments. */
 size_t pico_workspace_bytes(int64_t n, int64_t m, int algo);

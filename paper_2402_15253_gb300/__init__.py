@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
               L.pico_get_stats, L.pico_version):
         f.restype = i32
     L.pico_version.argtypes = []
+    L.pico_coreness_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+    L.pico_coreness_noalloc.restype = i32
     _lib = L
     return L
 
@@ -116,6 +118,19 @@ def pico_coreness(row_ptr, col_idx, n: int, m: int, out_core, algo: int, stream=
 def pico_coreness_i64(row_ptr, col_idx, n: int, m: int, out_core, algo: int, stream=None) -> int:
     return load().pico_coreness_i64(_ptr(row_ptr), _ptr(col_idx), n, m, _ptr(out_core), algo,
                                     _stream(stream))
+
+
+def pico_coreness_noalloc(row_ptr, col_idx, n: int, m: int, out_core, out_status=None,
+                          stream=None) -> int:
+    """PeelOne through the entry point that allocates no device memory, for
+    callers that cannot allocate while they run; graphs up to
+    PICO_NOALLOC_MAX_VERTICES vertices and PICO_NOALLOC_MAX_ARCS arcs."""
+    return load().pico_coreness_noalloc(_ptr(row_ptr), _ptr(col_idx), n, m, _ptr(out_core),
+                                        _ptr(out_status), _stream(stream))
+
+
+PICO_NOALLOC_MAX_VERTICES = 1 << 20
+PICO_NOALLOC_MAX_ARCS = 1 << 24
 
 
 def pico_workspace_bytes(n: int, m: int, algo: int) -> int:
