@@ -81,6 +81,32 @@ int pico_coreness_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n,
                       int32_t *out_core, int algo, pico_stream_t stream);
 
 /*
+ * Coreness of G independent graphs packed back to back, in one launch.
+ * Coreness is defined per graph (Sec. I), so the result equals G separate
+ * calls; each graph must satisfy the single-graph contract and may be empty.
+ *   vtx_off, arc_off: device int64 prefix offsets, G + 1 entries each
+ *     (vtx_off[0] == arc_off[0] == 0); graph g owns vertices
+ *     [vtx_off[g], vtx_off[g+1]) and arcs [arc_off[g], arc_off[g+1]).
+ *   row_ptr: device int32, graph-local offsets (relative to arc_off[g]);
+ *     graph g's n_g + 1 entries start at row_ptr[vtx_off[g] + g], so the
+ *     array holds vtx_off[G] + G entries.
+ *   col_idx: device int32, graph-local vertex ids, arc_off[G] entries.
+ *   total_vertices, total_arcs: must equal vtx_off[G] and arc_off[G] (the
+ *     host cannot read device memory without synchronising).
+ *   out_core: device int32, vtx_off[G] entries, each graph's coreness.
+ * One CTA solves one graph at a time, largest graphs first; a graph needs
+ * fewer than 2^31 arcs. G == 0 is a no-op.
+ */
+int pico_coreness_batched(const int64_t *vtx_off, const int64_t *arc_off, int32_t G,
+                          const int32_t *row_ptr, const int32_t *col_idx,
+                          int64_t total_vertices, int64_t total_arcs, int32_t *out_core,
+                          int algo, pico_stream_t stream);
+
+/* Scratch bytes a batched call with these totals allocates. */
+size_t pico_workspace_bytes_batched(int32_t G, int64_t total_vertices, int64_t total_arcs,
+                                    int algo);
+
+/*
  * PeelOne for callers that cannot allocate device memory. The paper has no
  * counterpart: this entry point exists for host code that must not call
  * cudaMalloc or any other allocating routine while it runs, for example a

@@ -82,6 +82,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
               L.pico_get_stats, L.pico_version):
         f.restype = i32
     L.pico_version.argtypes = []
+    L.pico_coreness_batched.argtypes = [vp, vp, i32, vp, vp, i64, i64, vp, i32, vp]
+    L.pico_coreness_batched.restype = i32
+    L.pico_workspace_bytes_batched.argtypes = [i32, i64, i64, i32]
+    L.pico_workspace_bytes_batched.restype = ctypes.c_size_t
     L.pico_coreness_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.pico_coreness_noalloc.restype = i32
     _lib = L
@@ -118,6 +122,17 @@ def pico_coreness(row_ptr, col_idx, n: int, m: int, out_core, algo: int, stream=
 def pico_coreness_i64(row_ptr, col_idx, n: int, m: int, out_core, algo: int, stream=None) -> int:
     return load().pico_coreness_i64(_ptr(row_ptr), _ptr(col_idx), n, m, _ptr(out_core), algo,
                                     _stream(stream))
+
+
+def pico_coreness_batched(vtx_off, arc_off, G: int, row_ptr, col_idx, total_vertices: int,
+                          total_arcs: int, out_core, algo: int, stream=None) -> int:
+    return load().pico_coreness_batched(_ptr(vtx_off), _ptr(arc_off), G, _ptr(row_ptr),
+                                        _ptr(col_idx), total_vertices, total_arcs,
+                                        _ptr(out_core), algo, _stream(stream))
+
+
+def pico_workspace_bytes_batched(G: int, total_vertices: int, total_arcs: int, algo: int) -> int:
+    return int(load().pico_workspace_bytes_batched(G, total_vertices, total_arcs, algo))
 
 
 def pico_coreness_noalloc(row_ptr, col_idx, n: int, m: int, out_core, out_status=None,
@@ -160,6 +175,32 @@ def pico_version() -> int:
 # ---------------------------------------------------------------------------
 # convenience
 # ---------------------------------------------------------------------------
+
+def coreness_batched(vtx_off: torch.Tensor, arc_off: torch.Tensor, row_ptr: torch.Tensor,
+                     col_idx: torch.Tensor, algo="peelone", total_vertices: int | None = None,
+                     total_arcs: int | None = None, out: torch.Tensor | None = None,
+                     stream=None, check: bool = True) -> torch.Tensor:
+    """Coreness of a packed batch (see pico_coreness_batched). The totals are
+    read from the offset tensors unless given (that read synchronises)."""
+    a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    G = vtx_off.numel() - 1
+    if total_vertices is None:
+        total_vertices = int(vtx_off[-1].item())
+    if total_arcs is None:
+        total_arcs = int(arc_off[-1].item())
+    if out is None:
+        out = torch.empty(total_vertices, dtype=torch.int32, device=row_ptr.device)
+    with torch.cuda.device(row_ptr.device):
+        rc = pico_coreness_batched(vtx_off, arc_off, G, row_ptr, col_idx, total_vertices,
+                                   total_arcs, out, a, stream)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_coreness_batched")
+        if check:
+            st = pico_last_device_status(stream)
+            if st != PICO_OK:
+                raise PicoError(st, "device")
+    return out
+
 
 def coreness(row_ptr: torch.Tensor, col_idx: torch.Tensor, algo="peelone",
              out: torch.Tensor | None = None, stream=None, check: bool = True) -> torch.Tensor:

@@ -1,0 +1,196 @@
+// Batched form: the coreness of G independent graphs in one launch.
+//
+// Coreness is defined per connected component (Sec. I: the k-core is a
+// maximal subgraph), so graphs packed side by side are solved independently.
+// One persistent CTA solves one graph at a time with the same algorithm
+// bodies as the single-graph kernels (peel::run, histo::run), synchronised by
+// __syncthreads with its counters in shared memory (CtaDom). CTAs take graphs
+// from a ticket counter in the order of a schedule that lists graphs by
+// decreasing arc count (power-of-two buckets), so the largest graphs start
+// first and the small ones fill in behind them.
+//
+// Scratch is sliced per graph: vertex-indexed arrays at vtx_off[g], the
+// histogram at arc_off[g], and chunk lists at arc_off[g] / 16 + 2g with
+// m_g / 16 + 2 entries (at least m_g / kChunk + m_g / (kSmallDeg + 1) + 2).
+#include "histocore.cuh"
+#include "peelone.cuh"
+#include "pico_launch.h"
+
+namespace pico {
+namespace {
+
+constexpr int kBuckets = 64;
+
+struct BatchParams {
+    const long long *vtx_off, *arc_off;
+    int G;
+    const int *rp, *ci;
+    int *core;
+    int *order;
+    int *res0, *res1, *qs;                          // PeelOne
+    int *oldcore, *histo, *lists[6], *us;           // HistoCore
+    int2 *chunks;                                   // both
+    Ctrl *ctl;
+};
+
+__device__ __forceinline__ int size_bucket(long long m)
+{
+    return m <= 0 ? 0 : 64 - __clzll(m);
+}
+
+// Lists the graphs by decreasing arc-count bucket (one CTA).
+__global__ void __launch_bounds__(1024) schedule_kernel(const long long *arc_off, int G, int *order)
+{
+    __shared__ unsigned cnt[kBuckets];
+    __shared__ unsigned start[kBuckets];
+    if (threadIdx.x < kBuckets) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int g = threadIdx.x; g < G; g += blockDim.x)
+        atomicAdd(&cnt[size_bucket(arc_off[g + 1] - arc_off[g])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int b = kBuckets - 1; b >= 0; --b) {
+            start[b] = run;
+            run += cnt[b];
+        }
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        const unsigned pos = atomicAdd(&start[size_bucket(arc_off[g + 1] - arc_off[g])], 1u);
+        order[pos] = g;
+    }
+}
+
+template <int Algo>
+__global__ void __launch_bounds__(kThreads, 2) batched_kernel(BatchParams bp, LastResult *last)
+{
+    __shared__ unsigned s_live[kLiveWords];
+    __shared__ unsigned s_snap[kLiveWords + 1];
+    __shared__ unsigned s_tmp[256];
+    __shared__ unsigned long long s_red[32];
+    __shared__ unsigned long long st[kStCount];
+    __shared__ int s_ticket;
+    if (threadIdx.x < kStCount) st[threadIdx.x] = 0;
+    __syncthreads();
+    CtaDom dom{bp.ctl, s_live, s_snap, 0u};
+    PhaseClock clk;
+    unsigned long long arcs = 0, atomics = 0, slots = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_ticket = (int)atomicAdd(&bp.ctl->live.w[0], 1u);
+        __syncthreads();
+        const int t = s_ticket;
+        __syncthreads();
+        if (t >= bp.G) break;
+        const int g = bp.order[t];
+        const long long v0 = bp.vtx_off[g], n = bp.vtx_off[g + 1] - v0;
+        const long long a0 = bp.arc_off[g], m = bp.arc_off[g + 1] - a0;
+        if (n <= 0) continue;
+        dom.reset();
+        int2 *chunks = bp.chunks + (a0 / 16 + 2ll * g);
+        const unsigned chunk_cap = (unsigned)(m / 16 + 2);
+        if (Algo == 0) {
+            peel::Params<int> p{bp.rp + v0 + g, bp.ci + a0,    n,      bp.core + v0,
+                                bp.res0 + v0,   bp.res1 + v0,  bp.qs + v0, chunks,
+                                chunk_cap,      bp.ctl};
+            peel::run(p, dom, s_tmp, st, clk, arcs, atomics);
+        } else {
+            histo::Params<int> p;
+            p.rp = bp.rp + v0 + g;
+            p.ci = bp.ci + a0;
+            p.n = n;
+            p.m = m;
+            p.core = bp.core + v0;
+            p.oldcore = bp.oldcore + v0;
+            p.histo = bp.histo + a0;
+            p.tl[0] = bp.lists[0] + v0;
+            p.wl[0] = bp.lists[1] + v0;
+            p.bl[0] = bp.lists[2] + v0;
+            p.tl[1] = bp.lists[3] + v0;
+            p.wl[1] = bp.lists[4] + v0;
+            p.bl[1] = bp.lists[5] + v0;
+            p.us = bp.us + v0;
+            p.ub = chunks;
+            p.ub_cap = chunk_cap;
+            p.ctl = bp.ctl;
+            p.zero_histo = true;
+            histo::run(p, dom, s_tmp, st, clk, arcs, atomics, slots);
+        }
+        __syncthreads();
+        if (status_of(bp.ctl) != 0) break;
+    }
+    block_sum_to(arcs, &bp.ctl->stats[kStArcs], s_red);
+    block_sum_to(atomics, &bp.ctl->stats[kStAtomics], s_red);
+    block_sum_to(slots, &bp.ctl->stats[kStSlots], s_red);
+    if (threadIdx.x == 0) {
+        atomicMax(&bp.ctl->stats[kStKmax], st[kStKmax]);
+        st[kStKmax] = 0;
+    }
+    finish_block(bp.ctl, last, Algo, st, kStCount);
+}
+
+}  // namespace
+
+size_t batched_ws_bytes(int G, long long total_n, long long total_m, int algo)
+{
+    Carver c(nullptr);
+    c.take<Ctrl>(1);
+    c.take<int>(G);
+    const size_t nchunks = (size_t)(total_m / 16 + 2ll * G + 2);
+    if (algo == 0) {
+        for (int i = 0; i < 3; ++i) c.take<int>(total_n);
+    } else {
+        c.take<int>(total_n);   // oldcore
+        c.take<int>(total_m);   // histo
+        for (int i = 0; i < 7; ++i) c.take<int>(total_n);
+    }
+    c.take<int2>(nchunks);
+    return c.size();
+}
+
+int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const int32_t *rp,
+                   const int32_t *ci, long long total_n, long long total_m, int32_t *core,
+                   int algo, void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg)
+{
+    Carver c(ws);
+    BatchParams bp{};
+    bp.vtx_off = reinterpret_cast<const long long *>(vtx_off);
+    bp.arc_off = reinterpret_cast<const long long *>(arc_off);
+    bp.G = G;
+    bp.rp = rp;
+    bp.ci = ci;
+    bp.core = core;
+    bp.ctl = c.take<Ctrl>(1);
+    bp.order = c.take<int>(G);
+    if (algo == 0) {
+        bp.res0 = c.take<int>(total_n);
+        bp.res1 = c.take<int>(total_n);
+        bp.qs = c.take<int>(total_n);
+    } else {
+        bp.oldcore = c.take<int>(total_n);
+        bp.histo = c.take<int>(total_m);
+        for (int i = 0; i < 6; ++i) bp.lists[i] = c.take<int>(total_n);
+        bp.us = c.take<int>(total_n);
+    }
+    bp.chunks = c.take<int2>((size_t)(total_m / 16 + 2ll * G + 2));
+    if (cudaMemsetAsync(bp.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
+    schedule_kernel<<<1, 1024, 0, stream>>>(bp.arc_off, G, bp.order);
+    if (cudaGetLastError() != cudaSuccess) return -3;
+
+    static int occ[2][64] = {};
+    int &o = occ[algo & 1][cfg.device & 63];
+    const void *fn = algo == 0 ? (const void *)batched_kernel<0> : (const void *)batched_kernel<1>;
+    if (o == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kThreads, 0) != cudaSuccess ||
+            o <= 0)
+            return -3;
+    }
+    const int ctas = cfg.sms * o;
+    const int grid = ctas < G ? ctas : G;
+    void *args[] = {&bp, &last};
+    if (cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, stream) != cudaSuccess)
+        return -3;
+    return 0;
+}
+
+}  // namespace pico

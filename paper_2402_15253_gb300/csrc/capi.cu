@@ -129,6 +129,46 @@ int pico_coreness_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n,
                                     out_core, algo, (cudaStream_t)stream);
 }
 
+int pico_coreness_batched(const int64_t *vtx_off, const int64_t *arc_off, int32_t G,
+                          const int32_t *row_ptr, const int32_t *col_idx,
+                          int64_t total_vertices, int64_t total_arcs, int32_t *out_core,
+                          int algo, pico_stream_t stream)
+{
+    if (G < 0 || total_vertices < 0 || total_arcs < 0 ||
+        (algo != PICO_ALGO_PEELONE && algo != PICO_ALGO_HISTOCORE))
+        return PICO_ERR_INVALID_ARG;
+    if (G == 0 || total_vertices == 0) return PICO_OK;
+    if (!vtx_off || !arc_off || !row_ptr || !out_core || (total_arcs > 0 && !col_idx))
+        return PICO_ERR_INVALID_ARG;
+    if (total_vertices >= (1ll << 40) || total_arcs >= (1ll << 40)) return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = pico::batched_ws_bytes(G, total_vertices, total_arcs, algo);
+    void *ws = nullptr;
+    if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_OOM;
+    }
+    rc = pico::launch_batched(vtx_off, arc_off, G, row_ptr, col_idx, total_vertices, total_arcs,
+                              out_core, algo, ws, d->last, s, d->cfg);
+    cudaFreeAsync(ws, s);
+    if (rc != 0) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    return PICO_OK;
+}
+
+size_t pico_workspace_bytes_batched(int32_t G, int64_t total_vertices, int64_t total_arcs,
+                                    int algo)
+{
+    if (G < 0 || total_vertices < 0 || total_arcs < 0) return 0;
+    if (algo != PICO_ALGO_PEELONE && algo != PICO_ALGO_HISTOCORE) return 0;
+    return pico::batched_ws_bytes(G, total_vertices, total_arcs, algo);
+}
+
 size_t pico_workspace_bytes(int64_t n, int64_t m, int algo)
 {
     if (n < 0 || m < 0) return 0;

@@ -1,268 +1,30 @@
-// PeelOne (Sec. III, Alg. 4) as one persistent cooperative kernel.
-//
-// core[] doubles as the residual degree and the coreness (Sec. III-C, step 2:
-// one array instead of deg[] + rem[]). Level k:
-//   scan    the compacted list of residual vertices is filtered: core == k
-//           -> frontier queue (Alg. 4 "scan"; Cor. 1 guarantees no residual
-//           vertex is below k), core > k -> kept for the next level, smaller
-//           values belong to vertices already peeled and are dropped. The
-//           smallest kept value is recorded so that an empty level jumps
-//           straight to the next non-empty one.
-//   scatter for each frontier vertex v and neighbour u with core[u] > k,
-//           core[u] is decremented atomically; the thread whose decrement
-//           takes u from k + 1 to k appends u to the frontier of the same
-//           level (the dynamic frontier of Sec. III-C, step 3). Each wave of
-//           the frontier ends with a grid barrier; the level ends when a wave
-//           appends nothing.
-//   repair  the clamp of atomicSub_{>=k} (Sec. III-B) is realised as a guard
-//           (core[u] > k, read before the atomic) plus an exact repair: a
-//           racing decrement can only hit a vertex already queued at level k
-//           (Thm. 1: its coreness is k), so after the level every vertex of
-//           the level's queue is written back to k. Values seen in between
-//           are only compared against k, where a dip below k and k itself
-//           give the same answer.
-// Every vertex is queued exactly once over the whole run (only one thread can
-// move it from k + 1 to k), so the queue is the peel order and needs n slots.
-#include "pico_device.cuh"
+// PeelOne (Sec. III, Alg. 4) on one graph as one persistent cooperative
+// kernel: the algorithm body is peel::run (peelone.cuh) over the whole grid.
+#include "peelone.cuh"
 #include "pico_launch.h"
 
 namespace pico {
 namespace {
 
-enum : int { L_QS = 0, L_QB = 1, L_KEPT = 2 /* 2..4 */, L_MIN = 5 /* 5..7 */ };
-
-constexpr int kScanItems = 4;   // residual-list entries per thread per scan step
-
 template <typename Off>
-struct PeelParams {
-    const Off *rp;
-    const int *ci;
-    long long n;
-    int *core;
-    int *res0, *res1;     // residual lists (ping-pong)
-    int *qs;              // queue of small vertices, n slots
-    int2 *qb;             // queue of (vertex, chunk) entries of large vertices
-    unsigned qb_cap;
-    Ctrl *ctl;
-    LastResult *last;
-    unsigned long long limit_ns;
-};
-
-template <typename Off>
-struct PeelArc {
-    const Off *rp;
-    int *core;
-    int *qs;
-    int2 *qb;
-    unsigned qb_cap;
-    Ctrl *ctl;
-    int k;
-    unsigned qs_cap;
-    unsigned long long n_arcs = 0, n_atomics = 0;
-
-    __device__ __forceinline__ void item(int, int &, int &) {}
-
-    __device__ __forceinline__ void arcs(const bool (&valid)[kU], const int (&)[kU],
-                                         const int (&u)[kU], const Off (&)[kU],
-                                         const int (&)[kU], const int (&)[kU])
-    {
-        int c[kU], old[kU];
-#pragma unroll
-        for (int j = 0; j < kU; ++j) c[j] = valid[j] ? ldcg(core + u[j]) : 0;
-#pragma unroll
-        for (int j = 0; j < kU; ++j) {
-            old[j] = 0;
-            if (valid[j]) {
-                ++n_arcs;
-                if (c[j] > k) {
-                    old[j] = atomicSub(core + u[j], 1);
-                    ++n_atomics;
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kU; ++j) {
-            // the decrement that moved u from k + 1 to k appends it (once)
-            const bool push = valid[j] && c[j] > k && old[j] == k + 1;
-            long long d = 0;
-            bool small = false, large = false;
-            if (push) {
-                d = (long long)(rp[u[j] + 1] - rp[u[j]]);
-                small = d <= kSmallDeg;
-                large = !small;
-            }
-            const unsigned pos = warp_push(&ctl->live.w[L_QS], small);
-            if (small) {
-                if (pos < qs_cap) qs[pos] = u[j];
-                else set_error(ctl, kErrNotConverged);
-            }
-            warp_push_chunks(large, u[j], d, qb, &ctl->live.w[L_QB], qb_cap, ctl);
-        }
-    }
-};
-
-template <typename Off>
-__device__ __forceinline__ void repair(const PeelParams<Off> &p, int k, unsigned s0, unsigned e0,
-                                       unsigned s1, unsigned e1, unsigned tid, unsigned nthreads)
-{
-    for (unsigned i = s0 + tid; i < e0; i += nthreads) p.core[ldcg(p.qs + i)] = k;
-    for (unsigned i = s1 + tid; i < e1; i += nthreads) p.core[__ldcg(&p.qb[i].x)] = k;
-}
-
-template <typename Off>
-__global__ void __launch_bounds__(kThreads, 2) peelone_kernel(PeelParams<Off> p)
+__global__ void __launch_bounds__(kThreads, 2)
+    peelone_kernel(peel::Params<Off> p, LastResult *last, unsigned long long limit_ns)
 {
     __shared__ unsigned s_snap[kLiveWords + 1];
     __shared__ unsigned s_tmp[128];
     __shared__ unsigned long long s_red[32];
-
-    Ctrl *ctl = p.ctl;
-    unsigned *live = ctl->live.w;
-    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned nthreads = gridDim.x * blockDim.x;
-    const unsigned gwarp = tid >> 5, nwarps = nthreads >> 5;
-    const long long n = p.n;
-    __shared__ unsigned long long st[kStCount];   // uniform statistics, thread 0 only
+    __shared__ unsigned long long st[kStCount];   // statistics, written by thread 0
     if (threadIdx.x < kStCount) st[threadIdx.x] = 0;
     __syncthreads();
     unsigned long long arcs = 0, atomics = 0;
     PhaseClock clk;
     clk.start();
-
-    // init: core = degree; residual list = non-isolated vertices
-    {
-        unsigned mx = 0;
-        for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += nthreads) {
-            const long long v = base + threadIdx.x;
-            bool keep = false;
-            if (v < n) {
-                const int d = (int)(p.rp[v + 1] - p.rp[v]);
-                p.core[v] = d;
-                keep = d > 0;
-                if (keep) mx = max(mx, (unsigned)(INT_MAX - d));
-            }
-            unsigned pos, unused;
-            block_push2(keep, false, &live[L_KEPT], &live[L_KEPT], pos, unused, s_tmp);
-            if (keep) p.res0[pos] = (int)v;
-        }
-        block_max_to(mx, &live[L_MIN], s_tmp);
-    }
-    if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-    if (threadIdx.x == 0) ++st[kStBarriers];
-    clk.end(st, kPhInit);
-    {
-        unsigned nres = s_snap[L_KEPT];
-        int k = INT_MAX - (int)s_snap[L_MIN];
-        unsigned slot = 1;   // kept/min slot of the next scan (slot 0: init)
-        int cur = 0;
-        int prev_k = -1;
-        unsigned r_s0 = 0, r_e0 = 0, r_s1 = 0, r_e1 = 0;
-        unsigned qs_tail = 0, qb_tail = 0;
-        long long scans = 0;
-        const long long max_scans = 2 * n + 4;
-
-        while (nres > 0) {
-            if (++scans > max_scans) {
-                if (threadIdx.x == 0) set_error(ctl, kErrNotConverged);
-                break;
-            }
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                live[L_KEPT + (slot + 1) % 3] = 0;
-                live[L_MIN + (slot + 1) % 3] = 0;
-            }
-            if (prev_k >= 0) repair(p, prev_k, r_s0, r_e0, r_s1, r_e1, tid, nthreads);
-            prev_k = -1;
-
-            // scan the residual list at level k (kScanItems vertices per thread)
-            const int *rin = cur ? p.res1 : p.res0;
-            int *rout = cur ? p.res0 : p.res1;
-            unsigned mx = 0;
-            const long long step = (long long)nthreads * kScanItems;
-            for (long long base = (long long)blockIdx.x * blockDim.x * kScanItems; base < nres;
-                 base += step) {
-                int v[kScanItems], c[kScanItems];
-                long long d[kScanItems];
-#pragma unroll
-                for (int j = 0; j < kScanItems; ++j) {
-                    const long long i = base + threadIdx.x + (long long)j * blockDim.x;
-                    v[j] = i < nres ? ldcg(rin + i) : -1;
-                }
-#pragma unroll
-                for (int j = 0; j < kScanItems; ++j) c[j] = v[j] >= 0 ? ldcg(p.core + v[j]) : -1;
-                unsigned nsmall = 0, nkeep = 0;
-#pragma unroll
-                for (int j = 0; j < kScanItems; ++j) {
-                    d[j] = 0;
-                    if (c[j] == k) d[j] = (long long)(p.rp[v[j] + 1] - p.rp[v[j]]);
-                    nsmall += (c[j] == k && d[j] <= kSmallDeg);
-                    nkeep += (c[j] > k);
-                    if (c[j] > k) mx = max(mx, (unsigned)(INT_MAX - c[j]));
-                }
-                unsigned pq, pk;
-                block_alloc2(nsmall, nkeep, &live[L_QS], &live[L_KEPT + slot], pq, pk, s_tmp);
-#pragma unroll
-                for (int j = 0; j < kScanItems; ++j) {
-                    if (c[j] == k && d[j] <= kSmallDeg) {
-                        if (pq < (unsigned)n) p.qs[pq] = v[j];
-                        else set_error(ctl, kErrNotConverged);
-                        ++pq;
-                    }
-                    if (c[j] > k) rout[pk++] = v[j];   // pk < nres <= n
-                }
-#pragma unroll
-                for (int j = 0; j < kScanItems; ++j)
-                    warp_push_chunks(c[j] == k && d[j] > kSmallDeg, v[j], d[j], p.qb, &live[L_QB],
-                                     p.qb_cap, ctl);
-            }
-            block_max_to(mx, &live[L_MIN + slot], s_tmp);
-            if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-            if (threadIdx.x == 0) ++st[kStBarriers];
-            if (threadIdx.x == 0) ++st[kStScans];
-            clk.end(st, kPhScan);
-
-            const unsigned qs0 = qs_tail, qb0 = qb_tail;
-            unsigned e0 = s_snap[L_QS], e1 = s_snap[L_QB];
-            nres = s_snap[L_KEPT + slot];
-            const int kmin_kept = INT_MAX - (int)s_snap[L_MIN + slot];
-            slot = (slot + 1) % 3;
-            cur ^= 1;
-            if (e0 == qs0 && e1 == qb0) {   // empty level: jump to the smallest kept value
-                k = kmin_kept;
-                continue;
-            }
-            if (threadIdx.x == 0) ++st[kStLevels];
-            if (threadIdx.x == 0) st[kStKmax] = (unsigned long long)k;
-
-            // scatter, wave by wave (dynamic frontier)
-            unsigned s0 = qs0, s1 = qb0;
-            while (s0 < e0 || s1 < e1) {
-                const unsigned units = (e0 - s0 + 31) / 32 + (e1 - s1);
-                PeelArc<Off> f{p.rp, p.core, p.qs, p.qb, p.qb_cap, ctl, k, (unsigned)n};
-                expand(p.rp, p.ci, p.qs + s0, e0 - s0, p.qb + s1, e1 - s1, gwarp, nwarps, f);
-                arcs += f.n_arcs;
-                atomics += f.n_atomics;
-                if (!grid_sync(ctl, s_snap, p.limit_ns)) goto done;
-                if (threadIdx.x == 0) ++st[kStBarriers];
-                if (threadIdx.x == 0) ++st[kStSubrounds];
-                clk.end(st, units < 64 ? kPhWaveTiny : (units < nwarps ? kPhWaveMid : kPhWaveWide));
-                s0 = e0;
-                s1 = e1;
-                e0 = s_snap[L_QS];
-                e1 = s_snap[L_QB];
-            }
-            qs_tail = e0;
-            qb_tail = e1;
-            prev_k = k;
-            r_s0 = qs0; r_e0 = e0; r_s1 = qb0; r_e1 = e1;
-            k = k + 1;
-        }
-        if (prev_k >= 0) repair(p, prev_k, r_s0, r_e0, r_s1, r_e1, tid, nthreads);
-    }
-done:
-    block_sum_to(arcs, &ctl->stats[kStArcs], s_red);
-    block_sum_to(atomics, &ctl->stats[kStAtomics], s_red);
+    GridDom dom{p.ctl, s_snap, limit_ns};
+    peel::run(p, dom, s_tmp, st, clk, arcs, atomics);
+    block_sum_to(arcs, &p.ctl->stats[kStArcs], s_red);
+    block_sum_to(atomics, &p.ctl->stats[kStAtomics], s_red);
     if (blockIdx.x != 0 && threadIdx.x < kStCount) st[threadIdx.x] = 0;
-    finish_block(ctl, p.last, 0, st, kStCount);
+    finish_block(p.ctl, last, 0, st, kStCount);
 }
 
 }  // namespace
@@ -288,7 +50,7 @@ int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *
                    LastResult *last, cudaStream_t stream, const LaunchCfg &cfg)
 {
     Carver c(ws);
-    PeelParams<Off> p;
+    peel::Params<Off> p;
     p.rp = rp;
     p.ci = ci;
     p.n = n;
@@ -299,20 +61,20 @@ int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *
     p.qs = c.take<int>(n);
     p.qb_cap = (unsigned)chunk_capacity(m);
     p.qb = c.take<int2>(p.qb_cap);
-    p.last = last;
-    p.limit_ns = cfg.limit_ns;
     if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
 
     static int occ[64] = {};
     int &o = occ[cfg.device & 63];
     if (o == 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, peelone_kernel<Off>, kThreads, 0) !=
-                cudaSuccess || o <= 0)
+                cudaSuccess ||
+            o <= 0)
             return -3;
     }
     const int per_sm = o < cfg.max_blocks_per_sm ? o : cfg.max_blocks_per_sm;
     dim3 grid(cfg.sms * per_sm), block(kThreads);
-    void *args[] = {&p};
+    unsigned long long limit = cfg.limit_ns;
+    void *args[] = {&p, &last, &limit};
     if (cudaLaunchCooperativeKernel((const void *)peelone_kernel<Off>, grid, block, args, 0,
                                     stream) != cudaSuccess)
         return -3;

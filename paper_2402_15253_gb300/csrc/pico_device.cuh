@@ -595,3 +595,61 @@ __device__ __forceinline__ void block_alloc2(unsigned n0, unsigned n1, unsigned 
 }
 
 }  // namespace pico
+
+namespace pico {
+
+// ---------------------------------------------------------------------------
+// synchronisation domains of the persistent kernels
+// ---------------------------------------------------------------------------
+// GridDom: the whole grid works on one graph; a phase ends with grid_sync and
+//   the counters live in the global control block.
+// CtaDom: one CTA works on one graph (the batched form); a phase ends with
+//   __syncthreads and the counters live in shared memory. The global status
+//   word is polled every 256 phases (loops are bounded regardless).
+// Both give every thread the counters as of the end of the last phase in
+// s_snap, and the loop geometry of the domain (thread rank, threads, CTAs).
+struct GridDom {
+    Ctrl *ctl;
+    unsigned *s_snap;
+    unsigned long long limit_ns;
+    static constexpr bool kGrid = true;
+    __device__ __forceinline__ unsigned *live() const { return ctl->live.w; }
+    __device__ __forceinline__ bool sync() { return grid_sync(ctl, s_snap, limit_ns); }
+    __device__ __forceinline__ unsigned tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ unsigned nthreads() const { return gridDim.x * blockDim.x; }
+    __device__ __forceinline__ unsigned cta() const { return blockIdx.x; }
+    __device__ __forceinline__ unsigned ncta() const { return gridDim.x; }
+    __device__ __forceinline__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+};
+
+struct CtaDom {
+    Ctrl *ctl;
+    unsigned *s_live;   // kLiveWords counters (shared memory)
+    unsigned *s_snap;   // kLiveWords + 1 words (shared memory)
+    unsigned nsync;
+    static constexpr bool kGrid = false;
+    // Zeroes the counters; every thread of the CTA calls it.
+    __device__ __forceinline__ void reset()
+    {
+        __syncthreads();
+        if (threadIdx.x < kLiveWords) s_live[threadIdx.x] = 0;
+        if (threadIdx.x == 0) s_snap[kLiveWords] = 0;
+        __syncthreads();
+    }
+    __device__ __forceinline__ unsigned *live() const { return s_live; }
+    __device__ __forceinline__ bool sync()
+    {
+        __syncthreads();
+        if (threadIdx.x < kLiveWords) s_snap[threadIdx.x] = s_live[threadIdx.x];
+        if (threadIdx.x == 0 && (++nsync & 255u) == 0) s_snap[kLiveWords] = (unsigned)status_of(ctl);
+        __syncthreads();
+        return s_snap[kLiveWords] == 0;
+    }
+    __device__ __forceinline__ unsigned tid() const { return threadIdx.x; }
+    __device__ __forceinline__ unsigned nthreads() const { return blockDim.x; }
+    __device__ __forceinline__ unsigned cta() const { return 0; }
+    __device__ __forceinline__ unsigned ncta() const { return 1; }
+    __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
+};
+
+}  // namespace pico

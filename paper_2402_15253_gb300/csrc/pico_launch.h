@@ -49,4 +49,10 @@ template <typename Off>
 int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int *core,
                      void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
 
+size_t batched_ws_bytes(int G, long long total_n, long long total_m, int algo);
+
+int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const int32_t *rp,
+                   const int32_t *ci, long long total_n, long long total_m, int32_t *core,
+                   int algo, void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
+
 }  // namespace pico
