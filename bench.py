@@ -167,6 +167,100 @@ def cpu_oracle_time(sample: str, repeats: int = 1):
     return edges, statistics.median(times)
 
 
+def bench_batched(pico, dev, stream, G: int, reps: int = 5):
+    """Graphs/s of the batched form on the packed 4,096-graph workload: one
+    plain launch, one launch replayed from a CUDA graph, and, as the
+    baseline, one single-graph launch per graph (PeelOne throughout; the
+    HistoCore batch is timed too). L2 is flushed before every timed launch."""
+    import torch
+    import graphgen as gg
+    pb = gg.batch_graph(G, gg.SEED_BASE + 4, device=dev)
+    tv, ta = int(pb.vtx_off[-1]), int(pb.arc_off[-1])
+    out = torch.empty(tv, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def batched(algo):
+        rc = pico.pico_coreness_batched(pb.vtx_off, pb.arc_off, G, pb.row_ptr, pb.col_idx, tv, ta,
+                                        out, pico.ALGOS[algo], stream)
+        if rc != 0:
+            raise pico.PicoError(rc, "batched")
+
+    def timed(fn):
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    res = {"workload": f"{G} graphs, log-uniform 100..200,000 vertices, half ER (mean degree "
+                       f"4-64), half R-MAT (edge factor 8-32); {tv} vertices, {ta} arcs",
+           "graphs": G, "vertices": tv, "arcs": ta}
+    for algo in ("peelone", "histocore"):
+        batched(algo)
+        if pico.pico_last_device_status(stream) != 0:
+            raise RuntimeError("batched warm-up failed")
+        ms = timed(lambda: batched(algo))
+        res[algo] = {"ms": ms, "graphs_per_s": G / (ms / 1e3), "edges_per_s": ta / 2 / (ms / 1e3)}
+    ref = out.clone()
+
+    # the same PeelOne batch replayed from a CUDA graph
+    torch.cuda.synchronize()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        batched("peelone")          # warm-up on the capture stream
+        cap.synchronize()
+        with torch.cuda.graph(graph, stream=cap):
+            rc = pico.pico_coreness_batched(pb.vtx_off, pb.arc_off, G, pb.row_ptr, pb.col_idx,
+                                            tv, ta, out, 0, cap)
+    torch.cuda.synchronize()
+    if rc != 0:
+        raise pico.PicoError(rc, "capture")
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    if not torch.equal(out, ref):
+        raise AssertionError("graph replay result differs")
+    ms_graph = timed(graph.replay)
+    res["peelone_graph_replay"] = {"ms": ms_graph, "graphs_per_s": G / (ms_graph / 1e3)}
+
+    # baseline: one single-graph launch per graph, all G graphs once
+    single = torch.empty_like(out)
+    vo = pb.vtx_off.cpu().tolist()
+    ao = pb.arc_off.cpu().tolist()
+    views = []
+    for g in range(G):
+        n = vo[g + 1] - vo[g]
+        views.append((pb.row_ptr[vo[g] + g: vo[g + 1] + g + 1], pb.col_idx[ao[g]:ao[g + 1]], n,
+                      ao[g + 1] - ao[g], single[vo[g]:vo[g + 1]]))
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for rp, ci, n, m, o in views:
+        rc = pico.pico_coreness(rp, ci, n, m, o, 0, stream)
+        if rc != 0:
+            raise pico.PicoError(rc, "single")
+    e1.record(stream)
+    e1.synchronize()
+    wall = time.perf_counter() - t0
+    ms_single = e0.elapsed_time(e1)
+    if not torch.equal(single, ref):
+        raise AssertionError("per-graph launches differ from the batch")
+    res["one_launch_per_graph"] = {"ms": ms_single, "wall_s": wall,
+                                   "graphs_per_s": G / (ms_single / 1e3)}
+    res["speedup_vs_one_launch_per_graph"] = ms_single / res["peelone"]["ms"]
+    res["speedup_graph_replay_vs_one_launch_per_graph"] = ms_single / ms_graph
+    return res
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -220,6 +314,8 @@ def main():
     ap.add_argument("--impl", default="pico", choices=["pico", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -375,6 +471,9 @@ def main():
             if not torch.equal(h_out[a], out["peelone"].cpu()):
                 raise AssertionError("e2e result differs")
         del d_rp, d_ci
+
+    if rank == 0 and not args.no_batched:
+        line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sample = CPU_SAMPLE.get(args.workload, args.workload)

@@ -134,6 +134,57 @@ size_t pico_workspace_bytes_batched(int32_t G, int64_t total_vertices, int64_t t
 int pico_coreness_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
                           int32_t *out_core, int32_t *out_status, pico_stream_t stream);
 
+/*
+ * Request server: continuous batching of coreness requests on the current
+ * device (the serving form; the paper has no counterpart). An engine thread
+ * admits arrived requests in arrival order while their device bytes (packed
+ * CSR, results and the batched call's scratch) fit in hbm_budget_bytes next
+ * to the requests already on the device, packs them into one micro-batch and
+ * solves it with one pico_coreness_batched launch on a free stream; up to
+ * `streams` micro-batches run at once, so requests that arrive while others
+ * run are admitted as slots and memory free up and overlap on the device.
+ * With single_graph = 1 each request is solved by its own pico_coreness call
+ * (with max_batch = 1 and streams = 1: the sequential plain path).
+ */
+typedef struct pico_server pico_server;
+
+typedef struct {
+    size_t hbm_budget_bytes; /* device bytes the admitted requests may hold */
+    int algo;                /* pico_algo used for every request */
+    int streams;             /* micro-batches in flight at once (1..64) */
+    int max_batch;           /* requests per micro-batch (>= 1) */
+    int single_graph;        /* 1: one single-graph call per request */
+} pico_server_config;
+
+/* Creates a server on the current device; NULL on invalid config or failure. */
+pico_server *pico_server_create(const pico_server_config *cfg);
+
+/*
+ * Submits one graph: host CSR (int32 row_ptr with n + 1 entries, int32
+ * col_idx with m entries) and a host buffer of n int32 for the result. The
+ * buffers must stay valid until the request completes and should be pinned
+ * (page-locked) so that copies overlap. arrival_ns (pico_clock_ns's clock):
+ * the request is not admitted before that time, so a recorded arrival
+ * process can be replayed. Returns the ticket (>= 0) or a negative status
+ * (PICO_ERR_OOM: the graph alone exceeds the budget).
+ */
+int64_t pico_server_submit(pico_server *server, const int32_t *row_ptr, const int32_t *col_idx,
+                           int64_t n, int64_t m, int32_t *out_core, int64_t arrival_ns);
+
+/* Moves up to cap completed tickets and their completion times
+   (pico_clock_ns) into the arrays; returns how many, or a negative status. */
+int pico_server_poll(pico_server *server, int64_t *tickets, int64_t *done_ns, int cap);
+
+/* Blocks until every submitted request has completed; returns the first
+   error seen by the engine (PICO_OK if none). */
+int pico_server_drain(pico_server *server);
+
+/* Stops the engine after the submitted requests complete and frees the server. */
+int pico_server_destroy(pico_server *server);
+
+/* Monotonic clock of the server, in nanoseconds. */
+int64_t pico_clock_ns(void);
+
 /* Scratch bytes a single-graph call with these sizes allocates (admission
    accounting). Returns 0 for invalid arguments. */
 size_t pico_workspace_bytes(int64_t n, int64_t m, int algo);

@@ -58,6 +58,12 @@ class pico_stats(ctypes.Structure):
         return d
 
 
+class pico_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("algo", ctypes.c_int),
+                ("streams", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("single_graph", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -86,6 +92,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_coreness_batched.restype = i32
     L.pico_workspace_bytes_batched.argtypes = [i32, i64, i64, i32]
     L.pico_workspace_bytes_batched.restype = ctypes.c_size_t
+    L.pico_server_create.argtypes = [ctypes.POINTER(pico_server_config)]
+    L.pico_server_create.restype = vp
+    L.pico_server_submit.argtypes = [vp, vp, vp, i64, i64, vp, i64]
+    L.pico_server_submit.restype = i64
+    L.pico_server_poll.argtypes = [vp, vp, vp, i32]
+    L.pico_server_poll.restype = i32
+    L.pico_server_drain.argtypes = [vp]
+    L.pico_server_drain.restype = i32
+    L.pico_server_destroy.argtypes = [vp]
+    L.pico_server_destroy.restype = i32
+    L.pico_clock_ns.argtypes = []
+    L.pico_clock_ns.restype = i64
     L.pico_coreness_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.pico_coreness_noalloc.restype = i32
     _lib = L
@@ -133,6 +151,33 @@ def pico_coreness_batched(vtx_off, arc_off, G: int, row_ptr, col_idx, total_vert
 
 def pico_workspace_bytes_batched(G: int, total_vertices: int, total_arcs: int, algo: int) -> int:
     return int(load().pico_workspace_bytes_batched(G, total_vertices, total_arcs, algo))
+
+
+def pico_server_create(hbm_budget_bytes: int, algo: int, streams: int = 4, max_batch: int = 256,
+                       single_graph: int = 0):
+    cfg = pico_server_config(hbm_budget_bytes, algo, streams, max_batch, single_graph)
+    return load().pico_server_create(ctypes.byref(cfg))
+
+
+def pico_server_submit(server, row_ptr, col_idx, n: int, m: int, out_core, arrival_ns: int) -> int:
+    return load().pico_server_submit(server, _ptr(row_ptr), _ptr(col_idx), n, m, _ptr(out_core),
+                                     arrival_ns)
+
+
+def pico_server_poll(server, tickets, done_ns, cap: int) -> int:
+    return load().pico_server_poll(server, _ptr(tickets), _ptr(done_ns), cap)
+
+
+def pico_server_drain(server) -> int:
+    return load().pico_server_drain(server)
+
+
+def pico_server_destroy(server) -> int:
+    return load().pico_server_destroy(server)
+
+
+def pico_clock_ns() -> int:
+    return load().pico_clock_ns()
 
 
 def pico_coreness_noalloc(row_ptr, col_idx, n: int, m: int, out_core, out_status=None,

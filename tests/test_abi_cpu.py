@@ -80,3 +80,12 @@ def test_binding_names_mirror_the_abi(lib):
     pico, _ = lib
     for name in declared_functions():
         assert hasattr(pico, name), name
+
+
+def test_server_rejects_invalid_configs_without_gpu(lib):
+    pico, _ = lib
+    assert not pico.pico_server_create(1 << 30, 5, 4, 64, 0)     # unknown method
+    assert not pico.pico_server_create(1 << 30, 0, 0, 64, 0)     # no streams
+    assert not pico.pico_server_create(1 << 30, 0, 4, 0, 0)      # empty batches
+    assert pico.pico_server_submit(None, None, None, 1, 0, None, 0) == pico.PICO_ERR_INVALID_ARG
+    assert pico.pico_server_drain(None) == pico.PICO_ERR_INVALID_ARG

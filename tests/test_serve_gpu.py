@@ -1,0 +1,86 @@
+"""The request server (continuous batching): every request's result is the
+same in the mix as alone, and equals the oracle's."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pico():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_15253_gb300 as p
+    torch.cuda.set_device(0)
+    return p
+
+
+def make_requests(count, seed, nmax=40000):
+    graphs = [gg.spec_graph(s) for s in gg.batch_specs(count - 2, seed, nmin=20, nmax=nmax)]
+    graphs.insert(3, gg.from_edge_list([], 5))            # no edges
+    graphs.append(gg.rmat_graph(16, 16, seed))            # one large outlier
+    reqs = []
+    for g in graphs:
+        rp = g.row_ptr.to(torch.int32).pin_memory()
+        ci = g.col_idx.pin_memory() if g.arcs else torch.zeros(1, dtype=torch.int32).pin_memory()
+        out = torch.full((max(g.n, 1),), -1, dtype=torch.int32).pin_memory()
+        reqs.append((g, rp, ci, out))
+    return reqs
+
+
+def serve(pico, reqs, algo, budget, streams=4, max_batch=64, single=0, spacing_ns=20000):
+    srv = pico.pico_server_create(budget, algo, streams, max_batch, single)
+    assert srv
+    t0 = pico.pico_clock_ns()
+    tickets = []
+    for i, (g, rp, ci, out) in enumerate(reqs):
+        t = pico.pico_server_submit(srv, rp, ci, g.n, g.arcs, out, t0 + i * spacing_ns)
+        assert t >= 0
+        tickets.append(t)
+    assert pico.pico_server_drain(srv) == 0
+    tk = torch.zeros(len(reqs), dtype=torch.int64)
+    dn = torch.zeros(len(reqs), dtype=torch.int64)
+    k = pico.pico_server_poll(srv, tk, dn, len(reqs))
+    assert k == len(reqs)
+    assert sorted(tk.tolist()) == tickets
+    assert (dn >= t0).all()
+    assert pico.pico_server_destroy(srv) == 0
+    return [out[:g.n].clone().numpy() for g, _, _, out in reqs]
+
+
+@pytest.mark.parametrize("algo", [0, 1])
+def test_results_same_alone_and_in_the_mix(pico, algo):
+    reqs = make_requests(120, 91)
+    mixed = serve(pico, reqs, algo, budget=8 << 30)
+    for (g, rp, ci, out), got in zip(reqs, mixed):
+        want = oracle.bz_coreness(g.row_ptr.numpy(), g.col_idx.numpy())
+        assert np.array_equal(got, want)
+    # the same requests, each alone (sequential plain path), give the same bytes
+    alone = serve(pico, reqs, algo, budget=8 << 30, streams=1, max_batch=1, single=1,
+                  spacing_ns=0)
+    for a, b in zip(alone, mixed):
+        assert np.array_equal(a, b)
+
+
+def test_tight_budget_admits_as_memory_frees(pico):
+    reqs = make_requests(40, 92, nmax=20000)
+    sizes = [pico.pico_workspace_bytes_batched(1, g.n, g.arcs, 0) + 16 * (g.n + g.arcs + 64)
+             for g, _, _, _ in reqs]
+    budget = max(sizes) * 2        # only a few requests fit on the device at once
+    got = serve(pico, reqs, 0, budget=budget, streams=3, max_batch=8, spacing_ns=0)
+    for (g, _, _, _), x in zip(reqs, got):
+        assert np.array_equal(x, oracle.bz_coreness(g.row_ptr.numpy(), g.col_idx.numpy()))
+
+
+def test_request_larger_than_budget_is_rejected(pico):
+    g = gg.rmat_graph(14, 16, 93)
+    rp = g.row_ptr.pin_memory()
+    ci = g.col_idx.pin_memory()
+    out = torch.zeros(g.n, dtype=torch.int32).pin_memory()
+    srv = pico.pico_server_create(1 << 20, 0, 2, 8, 0)
+    assert pico.pico_server_submit(srv, rp, ci, g.n, g.arcs, out, 0) == pico.PICO_ERR_OOM
+    assert pico.pico_server_destroy(srv) == 0
