@@ -261,6 +261,89 @@ def bench_batched(pico, dev, stream, G: int, reps: int = 5):
     return res
 
 
+def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int = 256,
+                budget_gb: float = 40.0):
+    """Served form: a Poisson stream of requests drawn from the batch size
+    distribution (log-uniform 100..200,000 vertices, half ER, half R-MAT)
+    plus 5% R-MAT scale 20 outliers, replayed open-loop into the request
+    server (continuous batching, 40 GB admission budget) at 0.5/0.8/0.95 of
+    its measured capacity, next to the sequential plain path (one
+    single-graph call per request, one at a time) at the same loads.
+    Latency = completion - arrival, host clock, including the host-to-device
+    copy of each CSR and the copy of its result back."""
+    import math
+    import torch
+    import graphgen as gg
+    import oracle
+
+    # pool of distinct request graphs on pinned host memory
+    specs = gg.batch_specs(pool_size, gg.SEED_BASE + 5)
+    n_out = max(1, pool_size // 20)
+    graphs = [gg.spec_graph(sp, device=dev) for sp in specs[:pool_size - n_out]]
+    graphs += [gg.rmat_graph(20, 16, gg.SEED_BASE + 50 + i, device=dev) for i in range(n_out)]
+    pool = []
+    for g in graphs:
+        rp = g.row_ptr.to(torch.int32).cpu().pin_memory()
+        ci = (g.col_idx if g.arcs else torch.zeros(1, dtype=torch.int32, device=dev)).cpu().pin_memory()
+        out = torch.zeros(max(g.n, 1), dtype=torch.int32).pin_memory()
+        pool.append((g.n, g.arcs, rp, ci, out))
+    regular, outliers = list(range(pool_size - n_out)), list(range(pool_size - n_out, pool_size))
+    pick = []
+    for i in range(requests):
+        u = gg.unit_int(gg.SEED_BASE + 5, gg.S_SERVE, 2 * i)
+        v = gg.unit_int(gg.SEED_BASE + 5, gg.S_SERVE, 2 * i + 1)
+        lst = outliers if u < 0.05 else regular
+        pick.append(lst[min(len(lst) - 1, int(v * len(lst)))])
+    expo = [-math.log(1.0 - gg.unit_int(gg.SEED_BASE + 5, gg.S_SERVE + 1, i))
+            for i in range(requests)]
+    budget = int(budget_gb * (1 << 30))
+
+    def run(rate, single):
+        cfg = (1, 1, 1) if single else (4, 512, 0)
+        srv = pico.pico_server_create(budget, 0, cfg[0], cfg[1], cfg[2])
+        if not srv:
+            raise RuntimeError("pico_server_create failed")
+        t0 = pico.pico_clock_ns() + 2_000_000
+        arr, t = [], 0.0
+        for i in range(requests):
+            if rate is not None:
+                t += expo[i] / rate
+            arr.append(t0 + int(t * 1e9))
+        for i, j in enumerate(pick):
+            n, m, rp, ci, out = pool[j]
+            if pico.pico_server_submit(srv, rp, ci, n, m, out, arr[i]) < 0:
+                raise RuntimeError("submit failed")
+        rc = pico.pico_server_drain(srv)
+        tk = torch.zeros(requests, dtype=torch.int64)
+        dn = torch.zeros(requests, dtype=torch.int64)
+        k = pico.pico_server_poll(srv, tk, dn, requests)
+        pico.pico_server_destroy(srv)
+        if rc != 0 or k != requests:
+            raise RuntimeError(f"server failed rc={rc} done={k}")
+        arr_t = torch.tensor(arr, dtype=torch.int64)[tk]
+        lat = (dn - arr_t).double() / 1e6
+        span = (int(dn.max()) - int(torch.tensor(arr).min())) / 1e9
+        return {"graphs_per_s": requests / span, "p50_ms": float(lat.quantile(0.5)),
+                "p99_ms": float(lat.quantile(0.99)), "mean_ms": float(lat.mean())}
+
+    capacity = run(None, False)["graphs_per_s"]
+    res = {"workload": f"{requests} requests, Poisson arrivals, pool of {pool_size} graphs "
+                       f"(log-uniform 100..200,000 vertices, half ER, half R-MAT; "
+                       f"{n_out} R-MAT scale 20 drawn with probability 0.05)",
+           "budget_gb": budget_gb, "capacity_graphs_per_s": capacity, "loads": {}}
+    for f in loads:
+        rate = f * capacity
+        res["loads"][str(f)] = {"offered_graphs_per_s": rate, "served": run(rate, False),
+                                "sequential_plain": run(rate, True)}
+    # the shared per-graph result buffers must hold the oracle's coreness
+    for j in (0, 1, pool_size - 1):
+        n, m, rp, ci, out = pool[j]
+        want = oracle.bz_coreness(rp.numpy().astype("int64"), ci.numpy()[:m])
+        if not (out[:n].numpy() == want).all():
+            raise AssertionError(f"served result of pool graph {j} differs from the oracle")
+    return res
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -316,6 +399,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="requests of the served-form measurement (0: skip)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -474,6 +559,8 @@ def main():
 
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)
+    if rank == 0 and args.serve_requests > 0:
+        line["served"] = bench_serve(pico, dev, args.serve_requests)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sample = CPU_SAMPLE.get(args.workload, args.workload)
