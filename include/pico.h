@@ -224,6 +224,16 @@ typedef struct {
 
 int pico_get_stats(pico_stream_t stream, pico_stats *out);
 
+/*
+ * Phase trace of the most recent single-graph call on the current device,
+ * recorded only when the environment variable PICO_TRACE=1 was set when the
+ * device was first used (it costs one store per phase). Synchronises
+ * `stream`, then writes up to cap entries of three int64 each: phase kind (as
+ * in pico_stats.phase_ns), work units of the phase (vertices or chunks), and
+ * its device time in ns. Returns the number of entries or a negative status.
+ */
+int pico_get_trace(pico_stream_t stream, int64_t *out, int cap);
+
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int pico_version(void);
 

@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_server_destroy.restype = i32
     L.pico_clock_ns.argtypes = []
     L.pico_clock_ns.restype = i64
+    L.pico_get_trace.argtypes = [vp, vp, i32]
+    L.pico_get_trace.restype = i32
     L.pico_coreness_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.pico_coreness_noalloc.restype = i32
     _lib = L
@@ -211,6 +213,17 @@ def pico_get_stats(stream=None) -> dict:
     if rc != PICO_OK:
         raise PicoError(rc, "pico_get_stats")
     return st.as_dict()
+
+
+def pico_get_trace(stream=None, cap: int = 8192) -> list:
+    """Phase trace of the last call (needs PICO_TRACE=1 before first use):
+    a list of (phase name, work units, device ms)."""
+    buf = torch.zeros(3 * cap, dtype=torch.int64)
+    k = load().pico_get_trace(_stream(stream), _ptr(buf), cap)
+    if k < 0:
+        raise PicoError(k, "pico_get_trace")
+    b = buf[:3 * k].view(-1, 3).tolist()
+    return [(PHASES[kind], units, ns / 1e6) for kind, units, ns in b]
 
 
 def pico_version() -> int:

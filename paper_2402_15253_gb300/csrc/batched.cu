@@ -29,6 +29,7 @@ struct BatchParams {
     int *order;
     int *res0, *res1, *qs;                          // PeelOne
     int *oldcore, *histo, *lists[6], *us;           // HistoCore
+    int2 *vinfo;
     int2 *chunks;                                   // both
     Ctrl *ctl;
 };
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(kThreads, 2) batched_kernel(BatchParams bp, La
             p.n = n;
             p.m = m;
             p.core = bp.core + v0;
+            p.vinfo = bp.vinfo + v0;
             p.oldcore = bp.oldcore + v0;
             p.histo = bp.histo + a0;
             p.tl[0] = bp.lists[0] + v0;
@@ -140,6 +142,7 @@ size_t batched_ws_bytes(int G, long long total_n, long long total_m, int algo)
     if (algo == 0) {
         for (int i = 0; i < 3; ++i) c.take<int>(total_n);
     } else {
+        c.take<int2>(total_n);  // vinfo
         c.take<int>(total_n);   // oldcore
         c.take<int>(total_m);   // histo
         for (int i = 0; i < 7; ++i) c.take<int>(total_n);
@@ -167,6 +170,7 @@ int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const 
         bp.res1 = c.take<int>(total_n);
         bp.qs = c.take<int>(total_n);
     } else {
+        bp.vinfo = c.take<int2>(total_n);
         bp.oldcore = c.take<int>(total_n);
         bp.histo = c.take<int>(total_m);
         for (int i = 0; i < 6; ++i) bp.lists[i] = c.take<int>(total_n);

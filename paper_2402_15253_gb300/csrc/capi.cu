@@ -1,5 +1,6 @@
 // The C ABI declared in include/pico.h: argument checks, per-device state,
 // stream-ordered scratch allocation and dispatch to the persistent kernels.
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -57,6 +58,12 @@ int device_state(DeviceState **out)
             return PICO_ERR_OOM;
         }
         if (cudaMemset(d.last, 0, sizeof(pico::LastResult)) != cudaSuccess) {
+            cudaGetLastError();
+            return PICO_ERR_CUDA;
+        }
+        const unsigned trace_on = env_ll("PICO_TRACE", 0) > 0 ? 1u : 0u;
+        if (cudaMemcpy(&d.last->trace_on, &trace_on, sizeof(unsigned), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
             cudaGetLastError();
             return PICO_ERR_CUDA;
         }
@@ -221,7 +228,8 @@ int pico_get_stats(pico_stream_t stream, pico_stats *out)
         return PICO_ERR_CUDA;
     }
     pico::LastResult h;
-    if (cudaMemcpy(&h, d->last, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpy(&h, d->last, offsetof(pico::LastResult, trace_len), cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
         cudaGetLastError();
         return PICO_ERR_CUDA;
     }
@@ -243,6 +251,37 @@ int pico_get_stats(pico_stream_t stream, pico_stats *out)
         out->phase_count[i] = (int64_t)h.stats[pico::kStPhaseCount + i];
     }
     return PICO_OK;
+}
+
+int pico_get_trace(pico_stream_t stream, int64_t *out, int cap)
+{
+    if (cap < 0 || (cap > 0 && !out)) return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    unsigned len = 0;
+    if (cudaMemcpy(&len, &d->last->trace_len, sizeof(len), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    const int k = (int)(len < (unsigned)cap ? len : (unsigned)cap);
+    if (k == 0) return 0;
+    static thread_local pico::TraceEntry buf[pico::kTraceCap];
+    if (cudaMemcpy(buf, d->last->trace, sizeof(pico::TraceEntry) * k, cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    for (int i = 0; i < k; ++i) {
+        out[3 * i] = buf[i].kind;
+        out[3 * i + 1] = buf[i].units;
+        out[3 * i + 2] = (int64_t)buf[i].ns;
+    }
+    return k;
 }
 
 int pico_version(void) { return 100; }

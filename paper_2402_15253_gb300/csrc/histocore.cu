@@ -18,6 +18,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     unsigned long long arcs = 0, atomics = 0, slots = 0;
     PhaseClock clk;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && last->trace_on) {
+        last->trace_len = 0;
+        clk.trace = last->trace;
+        clk.trace_len = &last->trace_len;
+    }
     clk.start();
     GridDom dom{p.ctl, s_snap, limit_ns};
     histo::run(p, dom, s_tmp, st, clk, arcs, atomics, slots);
@@ -34,6 +39,7 @@ size_t histocore_ws_bytes(long long n, long long m)
 {
     Carver c(nullptr);
     c.take<Ctrl>(1);
+    c.take<longlong2>(n);  // vinfo (sized for int64 offsets)
     c.take<int>(n);        // oldcore
     c.take<int>(m);        // histo
     for (int i = 0; i < 6; ++i) c.take<int>(n);
@@ -54,6 +60,7 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
     p.m = m;
     p.core = core;
     p.ctl = c.take<Ctrl>(1);
+    p.vinfo = reinterpret_cast<histo::VRec<Off> *>(c.take<longlong2>(n));
     p.oldcore = c.take<int>(n);
     p.histo = c.take<int>(m);
     for (int i = 0; i < 2; ++i) {

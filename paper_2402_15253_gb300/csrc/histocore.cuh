@@ -43,12 +43,30 @@ constexpr int kBlockK = 2048;   // K above which a CTA walks the histogram
 // live counters: V_cnt lists (T/W/B) per round parity, update lists, init chunks
 enum : int { L_T = 0, L_W = 1, L_B = 2, /* parity 1: 3..5 */ L_US = 6, L_UB = 7, L_IB = 8 };
 
+// Per-vertex record {estimate, histogram base (= row_ptr[v])}: UpdateHisto
+// needs both for every neighbour it edits, and one 8-byte (16-byte with int64
+// offsets) gather replaces two scattered 4-byte gathers from separate arrays.
+template <typename Off> struct VRecOf { using type = int2; };
+template <> struct VRecOf<long long> { using type = longlong2; };
+template <typename Off> using VRec = typename VRecOf<Off>::type;
+
+template <typename Off>
+__device__ __forceinline__ VRec<Off> make_vrec(int est, Off base);
+template <>
+__device__ __forceinline__ int2 make_vrec<int>(int est, int base) { return make_int2(est, base); }
+template <>
+__device__ __forceinline__ longlong2 make_vrec<long long>(int est, long long base)
+{
+    return make_longlong2(est, base);
+}
+
 template <typename Off>
 struct Params {
     const Off *rp;
     const int *ci;
     long long n, m;
-    int *core;
+    int *core;                    // output: coreness, written at the end
+    VRec<Off> *vinfo;             // n records {estimate, histogram base}
     int *oldcore;
     int *histo;                   // m slots (zeroed by run() when zero_histo)
     int *tl[2], *wl[2], *bl[2];   // V_cnt lists by class, per parity (n slots each)
@@ -63,30 +81,31 @@ __device__ __forceinline__ int kclass(int K) { return K <= kWarpK ? 0 : (K <= kB
 
 template <typename Off>
 struct InitArc {
-    const int *core;
+    static constexpr int kArcs = 4;
+    const VRec<Off> *vinfo;
     int *histo;
     unsigned long long n_arcs = 0;
-    __device__ __forceinline__ void item(int v, int &a, int &) { a = ldcg(core + v); }
-    __device__ __forceinline__ void arcs(const bool (&valid)[kU], const int (&)[kU],
-                                         const int (&u)[kU], const Off (&rs)[kU],
-                                         const int (&dv)[kU], const int (&)[kU])
+    __device__ __forceinline__ void item(int v, int &a, int &) { a = (int)__ldcg(vinfo + v).x; }
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&)[kArcs],
+                                         const int (&u)[kArcs], const Off (&rs)[kArcs],
+                                         const int (&dv)[kArcs], const int (&)[kArcs])
     {
-        int du[kU];
+        int du[kArcs];
 #pragma unroll
-        for (int j = 0; j < kU; ++j) du[j] = valid[j] ? ldcg(core + u[j]) : 0;
+        for (int j = 0; j < kArcs; ++j) du[j] = valid[j] ? (int)__ldcg(vinfo + u[j]).x : 0;
 #pragma unroll
-        for (int j = 0; j < kU; ++j)
+        for (int j = 0; j < kArcs; ++j)
             if (valid[j]) {
                 ++n_arcs;
-                atomicAdd(histo + rs[j] + (du[j] < dv[j] ? du[j] : dv[j]) - 1, 1);
+                red_add(histo + rs[j] + (du[j] < dv[j] ? du[j] : dv[j]) - 1, 1);
             }
     }
 };
 
 template <typename Off>
 struct UpdateArc {
-    const Off *rp;
-    int *core;
+    static constexpr int kArcs = 4;
+    const VRec<Off> *vinfo;
     const int *oldcore;
     int *histo;
     int *tl, *wl, *bl;
@@ -99,21 +118,23 @@ struct UpdateArc {
     __device__ __forceinline__ void item(int v, int &x, int &y)
     {
         x = ldcg(oldcore + v);
-        y = ldcg(core + v);
+        y = (int)__ldcg(vinfo + v).x;
     }
-    __device__ __forceinline__ void arcs(const bool (&valid)[kU], const int (&)[kU],
-                                         const int (&u)[kU], const Off (&)[kU],
-                                         const int (&x)[kU], const int (&y)[kU])
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&)[kArcs],
+                                         const int (&u)[kArcs], const Off (&)[kArcs],
+                                         const int (&x)[kArcs], const int (&y)[kArcs])
     {
-        int K[kU], old[kU];
-        Off ru[kU];
+        int K[kArcs], old[kArcs];
+        Off ru[kArcs];
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
-            K[j] = valid[j] ? ldcg(core + u[j]) : 0;
-            ru[j] = valid[j] ? rp[u[j]] : 0;
+        for (int j = 0; j < kArcs; ++j) {
+            VRec<Off> r = make_vrec<Off>(0, 0);
+            if (valid[j]) r = __ldcg(vinfo + u[j]);
+            K[j] = (int)r.x;
+            ru[j] = (Off)r.y;
         }
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
+        for (int j = 0; j < kArcs; ++j) {
             old[j] = 0;
             if (valid[j]) {
                 ++n_arcs;
@@ -121,16 +142,16 @@ struct UpdateArc {
                     if (x[j] >= K[j]) {   // slot K holds cnt: its old value decides the append
                         old[j] = atomicSub(histo + ru[j] + K[j] - 1, 1);
                     } else {              // slot x < K: no append can follow
-                        atomicSub(histo + ru[j] + x[j] - 1, 1);
+                        red_add(histo + ru[j] + x[j] - 1, -1);
                     }
-                    atomicAdd(histo + ru[j] + y[j] - 1, 1);
+                    red_add(histo + ru[j] + y[j] - 1, 1);
                     n_atomics += 2;
                 }
             }
         }
         unsigned *live = live_base + 3 * par;
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
+        for (int j = 0; j < kArcs; ++j) {
             const bool push = valid[j] && K[j] > y[j] && x[j] >= K[j] && old[j] == K[j];
             const int cls = kclass(K[j]);
             const unsigned p0 = warp_push(&live[L_T], push && cls == 0);
@@ -157,7 +178,7 @@ __device__ __forceinline__ long long sum_apply(const Params<Off> &p, int v, Off 
         set_error(p.ctl, kErrBadGraph);
         return -1;
     }
-    p.core[v] = h;
+    p.vinfo[v].x = h;
     p.oldcore[v] = K;
     p.histo[rs + h - 1] = sum;
     return (long long)(p.rp[v + 1] - rs);
@@ -190,8 +211,9 @@ template <typename Off>
 __device__ void sum_block(const Params<Off> &p, unsigned *live, int v, int *s,
                           unsigned long long &slots)
 {
-    const Off rs = p.rp[v];
-    const int K = ldcg(p.core + v);
+    const VRec<Off> rec = __ldcg(p.vinfo + v);
+    const Off rs = (Off)rec.y;
+    const int K = (int)rec.x;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int carry = 0;
     for (int top = K; top >= 1; top -= (int)blockDim.x) {
@@ -241,8 +263,9 @@ __device__ __forceinline__ void sum_warp(const Params<Off> &p, unsigned *live, i
                                          unsigned long long &slots)
 {
     const int lane = threadIdx.x & 31;
-    const Off rs = p.rp[v];
-    const int K = ldcg(p.core + v);
+    const VRec<Off> rec = __ldcg(p.vinfo + v);
+    const Off rs = (Off)rec.y;
+    const int K = (int)rec.x;
     int carry = 0;
     for (int top = K; top >= 1; top -= 32) {
         const int slot = top - lane;
@@ -274,8 +297,9 @@ template <typename Off>
 __device__ __forceinline__ long long sum_thread(const Params<Off> &p, int v,
                                                 unsigned long long &slots)
 {
-    const Off rs = p.rp[v];
-    const int K = ldcg(p.core + v);
+    const VRec<Off> rec = __ldcg(p.vinfo + v);
+    const Off rs = (Off)rec.y;
+    const int K = (int)rec.x;
     int sum = 0, k = K;
     for (; k >= 1; --k) {
         sum += ldcg(p.histo + rs + k - 1);
@@ -309,8 +333,9 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         const long long v = base + threadIdx.x;
         long long d = 0;
         if (v < n) {
-            d = (long long)(p.rp[v + 1] - p.rp[v]);
-            p.core[v] = (int)d;
+            const Off r0 = p.rp[v];
+            d = (long long)(p.rp[v + 1] - r0);
+            p.vinfo[v] = make_vrec<Off>((int)d, r0);
         }
         const unsigned nch = d > kSmallDeg ? (unsigned)((d + kChunk - 1) / kChunk) : 0u;
         const unsigned pos = block_alloc(nch, &live[L_IB], s_tmp);
@@ -325,7 +350,7 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
 
     // InitHisto
     {
-        InitArc<Off> f{p.core, p.histo};
+        InitArc<Off> f{p.vinfo, p.histo};
         expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, p.ub, snap[L_IB], gwarp, nwarps, f);
         arcs += f.n_arcs;
         atomics += f.n_arcs;
@@ -339,8 +364,9 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         const long long v = base + threadIdx.x;
         bool in[3] = {false, false, false};
         if (v < n) {
-            const int d = ldcg(p.core + v);
-            if (d >= 1 && ldcg(p.histo + p.rp[v] + d - 1) < d) in[kclass(d)] = true;
+            const VRec<Off> rec = __ldcg(p.vinfo + v);
+            const int d = (int)rec.x;
+            if (d >= 1 && ldcg(p.histo + (Off)rec.y + d - 1) < d) in[kclass(d)] = true;
         }
         unsigned *const ctr[3] = {&live[L_T], &live[L_W], &live[L_B]};
         unsigned pos[3];
@@ -396,7 +422,7 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         }
         if (!dom.sync()) return;
         if (threadIdx.x == 0) ++st[kStBarriers];
-        if (Dom::kGrid) clk.end(st, kPhSumHisto);
+        if (Dom::kGrid) clk.end(st, kPhSumHisto, nt + nwl + nb);
 
         // UpdateHisto over the changed vertices
         const unsigned nus = snap[L_US], nub = snap[L_UB];
@@ -406,16 +432,19 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         }
         {
             const int np = 1 - par;
-            UpdateArc<Off> f{p.rp,      p.core,     p.oldcore, p.histo, p.tl[np], p.wl[np],
-                             p.bl[np],  ctl,        live,      np,      (unsigned)n};
-            expand(p.rp, p.ci, p.us, nus, p.ub, nub, gwarp, nwarps, f);
+            UpdateArc<Off> f{p.vinfo, p.oldcore, p.histo, p.tl[np], p.wl[np], p.bl[np],
+                             ctl,     live,      np,      (unsigned)n};
+            expand(p.rp, p.ci, p.us, nus, p.ub, nub, gwarp, nwarps, f,
+                   batch_width(nus, nub, nwarps));
             arcs += f.n_arcs;
             atomics += f.n_atomics;
         }
         if (!dom.sync()) return;
         if (threadIdx.x == 0) ++st[kStBarriers];
-        if (Dom::kGrid) clk.end(st, kPhUpdateHisto);
+        if (Dom::kGrid) clk.end(st, kPhUpdateHisto, nus + nub);
     }
+    // the estimates are the coreness now (no vertex has cnt < estimate)
+    for (long long v = first + threadIdx.x; v < n; v += nthreads) p.core[v] = (int)__ldcg(p.vinfo + v).x;
 }
 
 }  // namespace histo

@@ -22,6 +22,7 @@
 // zero (the control block and the status record) on its stream before the
 // kernel runs. Calls whose work overlaps on the GPU (concurrent streams, or
 // host threads racing) would use the same array at once and must not happen.
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -36,7 +37,10 @@ constexpr long long kMaxN = PICO_NOALLOC_MAX_VERTICES;
 constexpr long long kMaxM = PICO_NOALLOC_MAX_ARCS;
 // Status record + PeelOne scratch for the limits above (16.4 MiB), rounded up.
 constexpr size_t kNoAllocScratchBytes = size_t(17) << 20;
-constexpr size_t kStatusBytes = 512;   // LastResult, padded to 256-byte alignment
+constexpr size_t kStatusBytes = 512;   // LastResult header, padded to 256-byte alignment
+// The status record's header (status, statistics, trace switch) must fit in
+// kStatusBytes; its trace array is never written by this entry point.
+static_assert(offsetof(pico::LastResult, trace) <= kStatusBytes, "status record too large");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -103,7 +107,7 @@ extern "C" int pico_coreness_noalloc(const int32_t *row_ptr, const int32_t *col_
     int rc = noalloc_device(&d);
     if (rc != PICO_OK) return rc;
     pico::LastResult *status = reinterpret_cast<pico::LastResult *>(d->scratch);
-    if (cudaMemsetAsync(status, 0, sizeof(pico::LastResult), s) != cudaSuccess) {
+    if (cudaMemsetAsync(status, 0, offsetof(pico::LastResult, trace), s) != cudaSuccess) {
         cudaGetLastError();
         return PICO_ERR_CUDA;
     }

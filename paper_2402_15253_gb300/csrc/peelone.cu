@@ -18,6 +18,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     unsigned long long arcs = 0, atomics = 0;
     PhaseClock clk;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && last->trace_on) {
+        last->trace_len = 0;
+        clk.trace = last->trace;
+        clk.trace_len = &last->trace_len;
+    }
     clk.start();
     GridDom dom{p.ctl, s_snap, limit_ns};
     peel::run(p, dom, s_tmp, st, clk, arcs, atomics);

@@ -51,6 +51,7 @@ struct Params {
 
 template <typename Off>
 struct Arc {
+    static constexpr int kArcs = 4;
     const Off *rp;
     int *core;
     int *qs;
@@ -64,15 +65,15 @@ struct Arc {
 
     __device__ __forceinline__ void item(int, int &, int &) {}
 
-    __device__ __forceinline__ void arcs(const bool (&valid)[kU], const int (&)[kU],
-                                         const int (&u)[kU], const Off (&)[kU],
-                                         const int (&)[kU], const int (&)[kU])
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&)[kArcs],
+                                         const int (&u)[kArcs], const Off (&)[kArcs],
+                                         const int (&)[kArcs], const int (&)[kArcs])
     {
-        int c[kU], old[kU];
+        int c[kArcs], old[kArcs];
 #pragma unroll
-        for (int j = 0; j < kU; ++j) c[j] = valid[j] ? ldcg(core + u[j]) : 0;
+        for (int j = 0; j < kArcs; ++j) c[j] = valid[j] ? ldcg(core + u[j]) : 0;
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
+        for (int j = 0; j < kArcs; ++j) {
             old[j] = 0;
             if (valid[j]) {
                 ++n_arcs;
@@ -83,7 +84,7 @@ struct Arc {
             }
         }
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
+        for (int j = 0; j < kArcs; ++j) {
             // the decrement that moved u from k + 1 to k appends it (once)
             const bool push = valid[j] && c[j] > k && old[j] == k + 1;
             long long d = 0;
@@ -215,7 +216,7 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
             ++st[kStBarriers];
             ++st[kStScans];
         }
-        if (Dom::kGrid) clk.end(st, kPhScan);
+        if (Dom::kGrid) clk.end(st, kPhScan, nres);
 
         const unsigned qs0 = qs_tail, qb0 = qb_tail;
         unsigned e0 = snap[L_QS], e1 = snap[L_QB];
@@ -237,7 +238,8 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
         while (s0 < e0 || s1 < e1) {
             const unsigned units = (e0 - s0 + 31) / 32 + (e1 - s1);
             Arc<Off> f{p.rp, p.core, p.qs, p.qb, p.qb_cap, ctl, live, k, (unsigned)n};
-            expand(p.rp, p.ci, p.qs + s0, e0 - s0, p.qb + s1, e1 - s1, gwarp, nwarps, f);
+            expand(p.rp, p.ci, p.qs + s0, e0 - s0, p.qb + s1, e1 - s1, gwarp, nwarps, f,
+                   batch_width(e0 - s0, e1 - s1, nwarps));
             arcs += f.n_arcs;
             atomics += f.n_atomics;
             if (!dom.sync()) return;
@@ -246,7 +248,8 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
                 ++st[kStSubrounds];
             }
             if (Dom::kGrid)
-                clk.end(st, units < 64 ? kPhWaveTiny : (units < nwarps ? kPhWaveMid : kPhWaveWide));
+                clk.end(st, units < 64 ? kPhWaveTiny : (units < nwarps ? kPhWaveMid : kPhWaveWide),
+                        units);
             s0 = e0;
             s1 = e1;
             e0 = snap[L_QS];

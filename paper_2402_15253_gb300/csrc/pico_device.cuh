@@ -63,13 +63,24 @@ struct Ctrl {
     unsigned long long stats[kStCount];
 };
 
-// Per-device record of the most recent call, read by pico_get_stats and
-// pico_last_device_status.
+// Phase trace (opt-in): one entry per phase of the most recent call.
+constexpr int kTraceCap = 8192;
+struct TraceEntry {
+    unsigned kind;            // PhaseKind
+    unsigned units;           // work units of the phase (vertices or chunks)
+    unsigned long long ns;    // device time of the phase
+};
+
+// Per-device record of the most recent call, read by pico_get_stats,
+// pico_last_device_status and pico_get_trace.
 struct LastResult {
     int status;               // sticky: first error since the last read
     int pad;
     long long algo;
     unsigned long long stats[kStCount];
+    unsigned trace_len;
+    unsigned trace_on;        // set by the host when PICO_TRACE is on
+    TraceEntry trace[kTraceCap];
 };
 
 // ---------------------------------------------------------------------------
@@ -82,19 +93,26 @@ __device__ __forceinline__ unsigned long long gtime()
     return t;
 }
 
-// Per-phase device time, kept by thread 0 of CTA 0 (the only writer).
+// Per-phase device time, kept by thread 0 of CTA 0 (the only writer); with
+// a trace record, every phase is also appended to it.
 struct PhaseClock {
     unsigned long long t_prev = 0;
+    TraceEntry *trace = nullptr;
+    unsigned *trace_len = nullptr;
     __device__ __forceinline__ void start()
     {
         if (blockIdx.x == 0 && threadIdx.x == 0) t_prev = gtime();
     }
-    __device__ __forceinline__ void end(unsigned long long *st, int kind)
+    __device__ __forceinline__ void end(unsigned long long *st, int kind, unsigned units = 0)
     {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const unsigned long long t = gtime();
             st[kStPhaseNs + kind] += t - t_prev;
             st[kStPhaseCount + kind] += 1;
+            if (trace && *trace_len < (unsigned)kTraceCap) {
+                trace[*trace_len] = TraceEntry{(unsigned)kind, units, t - t_prev};
+                ++*trace_len;
+            }
             t_prev = t;
         }
     }
@@ -334,33 +352,56 @@ __device__ __forceinline__ void warp_push_chunks(bool pred, int v, long long d, 
     }
 }
 
-// Arcs issued per lane per step of expand(): their loads and atomics are
-// independent, so up to kU memory round trips per lane are in flight.
+// Default number of arcs a lane issues per step of expand(): their loads and
+// atomics are independent, so that many memory round trips per lane are in
+// flight. A functor sets its own count as F::kArcs.
 constexpr int kU = 4;
 
-// Functor interface used by expand():
+// Fire-and-forget atomic add (a reduction: no value comes back, so the warp
+// does not wait for it).
+__device__ __forceinline__ void red_add(int *p, int v)
+{
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Functor interface used by expand() (U = F::kArcs):
 //   void item(int v, int &a, int &b)     per-vertex prologue (lane-local)
-//   void arcs(const bool (&valid)[kU], const int (&v)[kU], const int (&u)[kU],
-//             const Off (&rs)[kU], const int (&a)[kU], const int (&b)[kU])
+//   void arcs(const bool (&valid)[U], const int (&v)[U], const int (&u)[U],
+//             const Off (&rs)[U], const int (&a)[U], const int (&b)[U])
 //                                        called by ALL 32 lanes together with
-//                                        kU arcs (v -> u) per lane; rs = row_ptr[v]
+//                                        U arcs (v -> u) per lane; rs = row_ptr[v]
 // `small` lists small vertices (nullptr: the identity list 0..nsmall-1, where
 // vertices with degree > kSmallDeg are skipped because their chunks are in
 // `big`). `big` lists (vertex, chunk) pairs.
+// Small vertices per warp unit for a phase with nsmall small vertices and
+// nbig chunk units: 32 when there is enough work for every warp, otherwise
+// fewer (a power of two) so that the phase's units spread over more warps and
+// its longest unit, which bounds the phase, gets shorter.
+__device__ __forceinline__ unsigned batch_width(unsigned nsmall, unsigned nbig, unsigned nwarps)
+{
+    if (nsmall == 0) return 32u;
+    const unsigned free_warps = nwarps > nbig ? nwarps - nbig : 1u;
+    unsigned vb = 32u;
+    while (vb > 1u && (nsmall + vb - 1u) / vb < free_warps) vb >>= 1;
+    return vb;
+}
+
 template <typename Off, typename F>
 __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__restrict__ ci,
                                        const int *small, unsigned nsmall, const int2 *big,
-                                       unsigned nbig, unsigned gwarp, unsigned nwarps, F &f)
+                                       unsigned nbig, unsigned gwarp, unsigned nwarps, F &f,
+                                       unsigned vb = 32u)
 {
+    constexpr int U = F::kArcs;
     const int lane = threadIdx.x & 31;
-    const unsigned nbatch = (nsmall + 31u) / 32u;
+    const unsigned nbatch = (nsmall + vb - 1u) / vb;
     const unsigned total = nbatch + nbig;
     for (unsigned unit = gwarp; unit < total; unit += nwarps) {
         if (unit < nbatch) {
-            const unsigned idx = unit * 32u + lane;
+            const unsigned idx = unit * vb + lane;
             int v = -1, d = 0, a = 0, b = 0;
             Off rs = 0;
-            if (idx < nsmall) {
+            if ((unsigned)lane < vb && idx < nsmall) {
                 v = small ? ldcg(small + idx) : (int)idx;
                 rs = rp[v];
                 const Off dd = rp[v + 1] - rs;
@@ -377,12 +418,12 @@ __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__
             }
             const int excl = incl - d;
             const int T = __shfl_sync(kFull, incl, 31);
-            for (int base = 0; base < T; base += 32 * kU) {
-                bool valid[kU];
-                int vo[kU], u[kU], ao[kU], bo[kU];
-                Off rso[kU];
+            for (int base = 0; base < T; base += 32 * U) {
+                bool valid[U];
+                int vo[U], u[U], ao[U], bo[U];
+                Off rso[U];
 #pragma unroll
-                for (int j = 0; j < kU; ++j) {
+                for (int j = 0; j < U; ++j) {
                     const int fidx = base + 32 * j + lane;
                     int o = 0;
 #pragma unroll
@@ -408,12 +449,12 @@ __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__
             const Off t = (s + kChunk < re) ? s + kChunk : re;
             int a = 0, b = 0;
             f.item(v, a, b);
-            for (Off e0 = s; e0 < t; e0 += 32 * kU) {
-                bool valid[kU];
-                int vo[kU], u[kU], ao[kU], bo[kU];
-                Off rso[kU];
+            for (Off e0 = s; e0 < t; e0 += 32 * U) {
+                bool valid[U];
+                int vo[U], u[U], ao[U], bo[U];
+                Off rso[U];
 #pragma unroll
-                for (int j = 0; j < kU; ++j) {
+                for (int j = 0; j < U; ++j) {
                     const Off e = e0 + 32 * j + lane;
                     valid[j] = e < t;
                     u[j] = valid[j] ? __ldg(ci + e) : -1;
