@@ -67,10 +67,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {
+    "peelone": ("pico_device.cuh", "peelone.cuh", "peelone.cu"),
+    "histocore": ("pico_device.cuh", "histocore.cuh", "histocore.cu"),
+}
+
+
+def kernel_source_hash(method: str) -> str:
+    """Hash of the sources that define a method's kernel."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2402_15253_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for name in KERNEL_SOURCES[method]:
+        with open(os.path.join(ROOT, "paper_2402_15253_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -88,7 +95,7 @@ def recorded_traffic(workload: str, method: str, arcs: int):
         m_bytes = re.search(r"dram_bytes_per_launch\s*=\s*`?([0-9.eE+]+)", text)
         m_wl = re.search(r"workload\s*=\s*(\w+)", text)
         m_arcs = re.search(r"arcs\s*=\s*([0-9]+)", text)
-        if not (m_hash and m_bytes and m_wl and m_arcs) or m_hash.group(1) != kernel_source_hash():
+        if not (m_hash and m_bytes and m_wl and m_arcs) or m_hash.group(1) != kernel_source_hash(method):
             continue
         wl = m_wl.group(1)
         if wl == workload:
@@ -344,6 +351,22 @@ def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int
     return res
 
 
+def job_totals(local_ms: float, local_units: int, device=None):
+    """Whole-job time and work over the ranks of the current process group
+    (or this process alone): the slowest rank's time and the sum of the
+    units every rank processed. Each rank works on its own replica, so the
+    only communication is this reduction."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return local_ms, local_units
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -484,12 +507,7 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in step_ev]
     per = {a: [evs[k][2 * i].elapsed_time(evs[k][2 * i + 1]) for k in range(args.steps)]
            for i, a in enumerate(("peelone", "histocore"))}
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = 2 * m_und * args.steps * ws
+    total_ms, units = job_totals(sum(step_ms), 2 * m_und * args.steps, dev)
     value = units / (total_ms / 1000.0)
 
     # roofline of the dominant kernel: algorithm-neutral bytes B_min per launch

@@ -234,6 +234,20 @@ int pico_get_stats(pico_stream_t stream, pico_stats *out);
  */
 int pico_get_trace(pico_stream_t stream, int64_t *out, int cap);
 
+/*
+ * Self-test of device-side failure detection (no counterpart in the paper).
+ * Runs the grid barrier of the persistent kernels with one CTA that never
+ * arrives, so the other CTAs' bounded waits run out after limit_ms (1..10000)
+ * milliseconds; nothing faults or hangs. Synchronises `stream` and returns
+ * the device status the launch recorded: PICO_ERR_TIMEOUT when the failure
+ * path works. Clears the sticky status before and after.
+ * Environment: PICO_WAIT_LIMIT_MS sets the wait limit of the compute kernels
+ * (default 4000, read once per device); PICO_FAULT_ALLOC=1 makes every
+ * scratch allocation of the compute entry points fail with PICO_ERR_OOM
+ * (host-side fault injection for tests).
+ */
+int pico_selftest_wait_timeout(int limit_ms, pico_stream_t stream);
+
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int pico_version(void);
 

@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_server_destroy.restype = i32
     L.pico_clock_ns.argtypes = []
     L.pico_clock_ns.restype = i64
+    L.pico_selftest_wait_timeout.argtypes = [i32, vp]
+    L.pico_selftest_wait_timeout.restype = i32
     L.pico_get_trace.argtypes = [vp, vp, i32]
     L.pico_get_trace.restype = i32
     L.pico_coreness_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
@@ -224,6 +226,10 @@ def pico_get_trace(stream=None, cap: int = 8192) -> list:
         raise PicoError(k, "pico_get_trace")
     b = buf[:3 * k].view(-1, 3).tolist()
     return [(PHASES[kind], units, ns / 1e6) for kind, units, ns in b]
+
+
+def pico_selftest_wait_timeout(limit_ms: int, stream=None) -> int:
+    return load().pico_selftest_wait_timeout(limit_ms, _stream(stream))
 
 
 def pico_version() -> int:

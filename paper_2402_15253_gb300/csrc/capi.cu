@@ -80,6 +80,10 @@ int device_state(DeviceState **out)
     return PICO_OK;
 }
 
+// Host-side fault injection for tests: with PICO_FAULT_ALLOC=1 every
+// scratch allocation of the compute entry points is reported as failed.
+bool fault_alloc() { return env_ll("PICO_FAULT_ALLOC", 0) > 0; }
+
 template <typename Off>
 int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_t *out,
                   int algo, cudaStream_t stream)
@@ -104,7 +108,7 @@ int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_
     const size_t bytes = algo == PICO_ALGO_PEELONE ? pico::peelone_ws_bytes(n, m)
                                                    : pico::histocore_ws_bytes(n, m);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, bytes, stream) != cudaSuccess) {
+    if (fault_alloc() || cudaMallocAsync(&ws, bytes, stream) != cudaSuccess) {
         cudaGetLastError();
         return PICO_ERR_OOM;
     }
@@ -154,7 +158,7 @@ int pico_coreness_batched(const int64_t *vtx_off, const int64_t *arc_off, int32_
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = pico::batched_ws_bytes(G, total_vertices, total_arcs, algo);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
+    if (fault_alloc() || cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return PICO_ERR_OOM;
     }
@@ -282,6 +286,21 @@ int pico_get_trace(pico_stream_t stream, int64_t *out, int cap)
         out[3 * i + 2] = (int64_t)buf[i].ns;
     }
     return k;
+}
+
+int pico_selftest_wait_timeout(int limit_ms, pico_stream_t stream)
+{
+    if (limit_ms < 1 || limit_ms > 10000) return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    (void)pico_last_device_status(stream);   // start from a clean status
+    rc = pico::selftest_wait_timeout(d->last, limit_ms, (cudaStream_t)stream, d->cfg);
+    if (rc != 0) {
+        cudaGetLastError();
+        return rc == -2 ? PICO_ERR_OOM : PICO_ERR_CUDA;
+    }
+    return pico_last_device_status(stream);
 }
 
 int pico_version(void) { return 100; }

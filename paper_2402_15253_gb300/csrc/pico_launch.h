@@ -55,4 +55,6 @@ int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const 
                    const int32_t *ci, long long total_n, long long total_m, int32_t *core,
                    int algo, void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
 
+int selftest_wait_timeout(LastResult *last, int limit_ms, cudaStream_t stream, const LaunchCfg &cfg);
+
 }  // namespace pico

@@ -106,8 +106,10 @@ struct pico_server {
         }
         const size_t off_b = align256(sizeof(long long) * 2 * (G + 1));
         const size_t rp_b = align256(4 * (tn + G)), ci_b = align256(4 * tm);
-        if (cudaMallocAsync(&b.dev, off_b + rp_b + ci_b + align256(4 * tn), s) != cudaSuccess)
+        if (cudaMallocAsync(&b.dev, off_b + rp_b + ci_b + align256(4 * tn), s) != cudaSuccess) {
+            b.dev = nullptr;
             return PICO_ERR_OOM;
+        }
         char *base = static_cast<char *>(b.dev);
         long long *d_off = reinterpret_cast<long long *>(base);
         int32_t *d_rp = reinterpret_cast<int32_t *>(base + off_b);
@@ -156,6 +158,7 @@ struct pico_server {
         }
         if (cudaEventRecord(b.done, s) != cudaSuccess) return PICO_ERR_CUDA;
         cudaFreeAsync(b.dev, s);
+        b.dev = nullptr;
         return PICO_OK;
     }
 
@@ -222,6 +225,8 @@ struct pico_server {
                     if (rc != PICO_OK) {
                         if (error == PICO_OK) error = rc;
                         cudaGetLastError();
+                        if (b.dev) cudaFreeAsync(b.dev, streams[b.slot]);
+                        b.dev = nullptr;
                         cudaEventRecord(b.done, streams[b.slot]);
                     }
                     inflight.push_back(std::move(b));
