@@ -204,10 +204,19 @@ def bench_batched(pico, dev, stream, G: int, reps: int = 5):
             ms.append(e0.elapsed_time(e1))
         return statistics.median(ms)
 
+    from paper_2402_15253_gb300 import autotune
+    pico.pico_set_tuning(*autotune.DEFAULT)
+    best_peel, timings = autotune.tune_batched(pico, pb.vtx_off, pb.arc_off, pb.row_ptr, pb.col_idx,
+                                               "peelone", reps=2, use_cache=False)
+    tuned = {"peelone": best_peel, "histocore": autotune.DEFAULT}
     res = {"workload": f"{G} graphs, log-uniform 100..200,000 vertices, half ER (mean degree "
                        f"4-64), half R-MAT (edge factor 8-32); {tv} vertices, {ta} arcs",
            "graphs": G, "vertices": tv, "arcs": ta}
+    res["tuning"] = {a: {"small_deg": t[0], "chunk": t[1], "cta_threads": t[2]}
+                     for a, t in tuned.items()}
+    res["peelone_default_tuning_ms"] = timings[autotune.DEFAULT]
     for algo in ("peelone", "histocore"):
+        pico.pico_set_tuning(*tuned[algo])
         batched(algo)
         if pico.pico_last_device_status(stream) != 0:
             raise RuntimeError("batched warm-up failed")
@@ -216,6 +225,7 @@ def bench_batched(pico, dev, stream, G: int, reps: int = 5):
     ref = out.clone()
 
     # the same PeelOne batch replayed from a CUDA graph
+    pico.pico_set_tuning(*tuned["peelone"])
     torch.cuda.synchronize()
     cap = torch.cuda.Stream()
     cap.wait_stream(torch.cuda.current_stream())
@@ -457,8 +467,15 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    # degree-class tuning per method, picked by the library's autotuner on this graph
+    from paper_2402_15253_gb300 import autotune
+    tuned = {}
+    for a in ("peelone", "histocore"):
+        tuned[a], _ = autotune.tune_single(pico, rp, ci, a, reps=2, use_cache=False)
+
     def step(ev=None):
         for i, a in enumerate(("peelone", "histocore")):
+            pico.pico_set_tuning(*tuned[a])
             if ev is not None:
                 ev[2 * i].record(stream)
             rc = (pico.pico_coreness if w_r == 4 else pico.pico_coreness_i64)(
@@ -476,6 +493,7 @@ def main():
         raise pico.PicoError(st, "warm-up")
     stats = {}
     for a in ("peelone", "histocore"):
+        pico.pico_set_tuning(*tuned[a])
         pico.coreness(rp, ci, a, out=out[a])
         stats[a] = pico.pico_get_stats(stream)
     kmax = int(out["peelone"].max().item())
@@ -539,6 +557,7 @@ def main():
                      "traffic_source": traffic_src,
                      "bytes_per_launch": b_min, "peak_kind": peak_kind,
                      "bytes_model": "B_min = w_r(n+1) + 8 B/arc + 4 B/vertex"},
+        "tuning": {a: {"small_deg": t[0], "chunk": t[1]} for a, t in tuned.items()},
         "methods": methods,
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
@@ -561,6 +580,7 @@ def main():
             d_rp.copy_(h_rp, non_blocking=True)
             d_ci.copy_(h_ci, non_blocking=True)
             for a in out:
+                pico.pico_set_tuning(*tuned[a])
                 pico.coreness(d_rp, d_ci, a, out=out[a], check=False)
                 h_out[a].copy_(out[a], non_blocking=True)
         e1.record(stream)

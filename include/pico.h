@@ -113,7 +113,7 @@ size_t pico_workspace_bytes_batched(int32_t G, int64_t total_vertices, int64_t t
  * service that reserved its whole device-memory budget at start-up, or an
  * embedding framework that owns every allocation. It computes what
  * pico_coreness(..., PICO_ALGO_PEELONE, ...) computes, allocates nothing, and
- * takes its scratch from one array compiled into the library: 17 MiB of
+ * takes its scratch from one array compiled into the library: 19 MiB of
  * device memory that every GPU on which the library is loaded holds until
  * the process exits.
  *
@@ -247,6 +247,18 @@ int pico_get_trace(pico_stream_t stream, int64_t *out, int cap);
  * (host-side fault injection for tests).
  */
 int pico_selftest_wait_timeout(int limit_ms, pico_stream_t stream);
+
+/*
+ * Degree-class work assignment of the current device's kernels (set by the
+ * autotuner, paper_2402_15253_gb300/autotune.py): vertices of degree at most
+ * small_deg (32..256) are batched 32 per warp; larger ones are split into
+ * chunks of `chunk` arcs (64..4096), one per warp; batched_threads (256 or
+ * 512) is the CTA size of the batched kernel (one CTA per graph). Applies to
+ * later calls on the device; defaults 32, 256, 512. Results never depend on
+ * these values, only the speed does.
+ */
+int pico_set_tuning(int small_deg, int chunk, int batched_threads);
+int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads);
 
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int pico_version(void);

@@ -11,7 +11,8 @@
 //
 // Scratch is sliced per graph: vertex-indexed arrays at vtx_off[g], the
 // histogram at arc_off[g], and chunk lists at arc_off[g] / 16 + 2g with
-// m_g / 16 + 2 entries (at least m_g / kChunk + m_g / (kSmallDeg + 1) + 2).
+// m_g / 16 + 2 entries (at least m_g / chunk + m_g / (small_deg + 1) + 2 for
+// every allowed tuning: chunk >= 64 and small_deg >= 32).
 #include "histocore.cuh"
 #include "peelone.cuh"
 #include "pico_launch.h"
@@ -32,6 +33,7 @@ struct BatchParams {
     int2 *vinfo;
     int2 *chunks;                                   // both
     Ctrl *ctl;
+    Tuning tn;
 };
 
 __device__ __forceinline__ int size_bucket(long long m)
@@ -63,8 +65,9 @@ __global__ void __launch_bounds__(1024) schedule_kernel(const long long *arc_off
     }
 }
 
-template <int Algo>
-__global__ void __launch_bounds__(kThreads, 2) batched_kernel(BatchParams bp, LastResult *last)
+template <int Algo, int Threads>
+__global__ void __launch_bounds__(Threads, 512 / Threads * 2)
+    batched_kernel(BatchParams bp, LastResult *last)
 {
     __shared__ unsigned s_live[kLiveWords];
     __shared__ unsigned s_snap[kLiveWords + 1];
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, 2) batched_kernel(BatchParams bp, La
         if (Algo == 0) {
             peel::Params<int> p{bp.rp + v0 + g, bp.ci + a0,    n,      bp.core + v0,
                                 bp.res0 + v0,   bp.res1 + v0,  bp.qs + v0, chunks,
-                                chunk_cap,      bp.ctl};
+                                chunk_cap,      bp.ctl,        bp.tn};
             peel::run(p, dom, s_tmp, st, clk, arcs, atomics);
         } else {
             histo::Params<int> p;
@@ -116,6 +119,7 @@ __global__ void __launch_bounds__(kThreads, 2) batched_kernel(BatchParams bp, La
             p.ub_cap = chunk_cap;
             p.ctl = bp.ctl;
             p.zero_histo = true;
+            p.tn = bp.tn;
             histo::run(p, dom, s_tmp, st, clk, arcs, atomics, slots);
         }
         __syncthreads();
@@ -177,22 +181,27 @@ int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const 
         bp.us = c.take<int>(total_n);
     }
     bp.chunks = c.take<int2>((size_t)(total_m / 16 + 2ll * G + 2));
+    bp.tn = cfg.tn;
     if (cudaMemsetAsync(bp.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
     schedule_kernel<<<1, 1024, 0, stream>>>(bp.arc_off, G, bp.order);
     if (cudaGetLastError() != cudaSuccess) return -3;
 
-    static int occ[2][64] = {};
-    int &o = occ[algo & 1][cfg.device & 63];
-    const void *fn = algo == 0 ? (const void *)batched_kernel<0> : (const void *)batched_kernel<1>;
+    const int threads = cfg.batched_threads == 256 ? 256 : 512;
+    const int vi = (algo & 1) * 2 + (threads == 256 ? 1 : 0);
+    static int occ[4][64] = {};
+    int &o = occ[vi][cfg.device & 63];
+    const void *fns[4] = {(const void *)batched_kernel<0, 512>, (const void *)batched_kernel<0, 256>,
+                          (const void *)batched_kernel<1, 512>, (const void *)batched_kernel<1, 256>};
+    const void *fn = fns[vi];
     if (o == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kThreads, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, 0) != cudaSuccess ||
             o <= 0)
             return -3;
     }
     const int ctas = cfg.sms * o;
     const int grid = ctas < G ? ctas : G;
     void *args[] = {&bp, &last};
-    if (cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, stream) != cudaSuccess)
+    if (cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, stream) != cudaSuccess)
         return -3;
     return 0;
 }

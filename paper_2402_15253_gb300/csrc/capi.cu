@@ -53,6 +53,8 @@ int device_state(DeviceState **out)
         d.cfg.sms = prop.multiProcessorCount;
         d.cfg.max_blocks_per_sm = (int)env_ll("PICO_BLOCKS_PER_SM", 2);
         d.cfg.limit_ns = (unsigned long long)env_ll("PICO_WAIT_LIMIT_MS", 4000) * 1000000ull;
+        d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk};
+        d.cfg.batched_threads = pico::kThreads;
         if (cudaMalloc(&d.last, sizeof(pico::LastResult)) != cudaSuccess) {
             cudaGetLastError();
             return PICO_ERR_OOM;
@@ -78,6 +80,14 @@ int device_state(DeviceState **out)
     }
     *out = &d;
     return PICO_OK;
+}
+
+// Launch configuration of a device, copied under the lock (pico_set_tuning
+// may change it from another thread).
+pico::LaunchCfg cfg_of(const DeviceState *d)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    return d->cfg;
 }
 
 // Host-side fault injection for tests: with PICO_FAULT_ALLOC=1 every
@@ -113,8 +123,8 @@ int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_
         return PICO_ERR_OOM;
     }
     rc = algo == PICO_ALGO_PEELONE
-             ? pico::launch_peelone<Off>(rp, ci, n, m, out, ws, d->last, stream, d->cfg)
-             : pico::launch_histocore<Off>(rp, ci, n, m, out, ws, d->last, stream, d->cfg);
+             ? pico::launch_peelone<Off>(rp, ci, n, m, out, ws, d->last, stream, cfg_of(d))
+             : pico::launch_histocore<Off>(rp, ci, n, m, out, ws, d->last, stream, cfg_of(d));
     cudaFreeAsync(ws, stream);
     if (rc != 0) {
         cudaGetLastError();
@@ -163,7 +173,7 @@ int pico_coreness_batched(const int64_t *vtx_off, const int64_t *arc_off, int32_
         return PICO_ERR_OOM;
     }
     rc = pico::launch_batched(vtx_off, arc_off, G, row_ptr, col_idx, total_vertices, total_arcs,
-                              out_core, algo, ws, d->last, s, d->cfg);
+                              out_core, algo, ws, d->last, s, cfg_of(d));
     cudaFreeAsync(ws, s);
     if (rc != 0) {
         cudaGetLastError();
@@ -295,12 +305,40 @@ int pico_selftest_wait_timeout(int limit_ms, pico_stream_t stream)
     int rc = device_state(&d);
     if (rc != PICO_OK) return rc;
     (void)pico_last_device_status(stream);   // start from a clean status
-    rc = pico::selftest_wait_timeout(d->last, limit_ms, (cudaStream_t)stream, d->cfg);
+    rc = pico::selftest_wait_timeout(d->last, limit_ms, (cudaStream_t)stream, cfg_of(d));
     if (rc != 0) {
         cudaGetLastError();
         return rc == -2 ? PICO_ERR_OOM : PICO_ERR_CUDA;
     }
     return pico_last_device_status(stream);
+}
+
+int pico_set_tuning(int small_deg, int chunk, int batched_threads)
+{
+    if (small_deg < pico::kMinSmallDeg || small_deg > pico::kMaxSmallDeg ||
+        chunk < pico::kMinChunk || chunk > pico::kMaxChunk ||
+        (batched_threads != 256 && batched_threads != 512))
+        return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_mu);
+    d->cfg.tn = pico::Tuning{small_deg, chunk};
+    d->cfg.batched_threads = batched_threads;
+    return PICO_OK;
+}
+
+int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads)
+{
+    if (!small_deg || !chunk || !batched_threads) return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_mu);
+    *small_deg = d->cfg.tn.small_deg;
+    *chunk = d->cfg.tn.chunk;
+    *batched_threads = d->cfg.batched_threads;
+    return PICO_OK;
 }
 
 int pico_version(void) { return 100; }

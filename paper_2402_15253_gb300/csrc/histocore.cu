@@ -72,6 +72,7 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
     p.ub_cap = (unsigned)chunk_capacity(m);
     p.ub = c.take<int2>(p.ub_cap);
     p.zero_histo = false;
+    p.tn = cfg.tn;
     if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
     if (m > 0 && cudaMemsetAsync(p.histo, 0, (size_t)m * sizeof(int), stream) != cudaSuccess)
         return -3;

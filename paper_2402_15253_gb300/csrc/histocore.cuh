@@ -75,6 +75,7 @@ struct Params {
     unsigned ub_cap;
     Ctrl *ctl;                    // status word (errors)
     bool zero_histo;
+    Tuning tn;
 };
 
 __device__ __forceinline__ int kclass(int K) { return K <= kWarpK ? 0 : (K <= kBlockK ? 1 : 2); }
@@ -190,11 +191,11 @@ __device__ __forceinline__ void list_changed(const Params<Off> &p, unsigned *liv
                                              long long d)
 {
     if (d < 0) return;
-    if (d <= kSmallDeg) {
+    if (d <= p.tn.small_deg) {
         const unsigned pos = atomicAdd(&live[L_US], 1u);
         if (pos < (unsigned)p.n) p.us[pos] = v;
         else set_error(p.ctl, kErrNotConverged);
-    } else if (!push_chunks(v, d, p.ub, &live[L_UB], p.ub_cap)) {
+    } else if (!push_chunks(v, d, p.ub, &live[L_UB], p.ub_cap, p.tn.chunk)) {
         set_error(p.ctl, kErrNotConverged);
     }
 }
@@ -337,7 +338,8 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
             d = (long long)(p.rp[v + 1] - r0);
             p.vinfo[v] = make_vrec<Off>((int)d, r0);
         }
-        const unsigned nch = d > kSmallDeg ? (unsigned)((d + kChunk - 1) / kChunk) : 0u;
+        const unsigned nch =
+            d > p.tn.small_deg ? (unsigned)((d + p.tn.chunk - 1) / p.tn.chunk) : 0u;
         const unsigned pos = block_alloc(nch, &live[L_IB], s_tmp);
         if (nch && (unsigned long long)pos + nch <= p.ub_cap)
             for (unsigned c = 0; c < nch; ++c) p.ub[pos + c] = make_int2((int)v, (int)c);
@@ -351,7 +353,8 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
     // InitHisto
     {
         InitArc<Off> f{p.vinfo, p.histo};
-        expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, p.ub, snap[L_IB], gwarp, nwarps, f);
+        expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, p.ub, snap[L_IB], gwarp, nwarps, f,
+               p.tn);
         arcs += f.n_arcs;
         atomics += f.n_arcs;
     }
@@ -411,14 +414,14 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
                 v = ldcg(p.tl[par] + i);
                 d = sum_thread(p, v, slots);
             }
-            const bool small = d >= 0 && d <= kSmallDeg;
+            const bool small = d >= 0 && d <= p.tn.small_deg;
             unsigned pos, unused;
             block_push2(small, false, &live[L_US], &live[L_US], pos, unused, s_tmp);
             if (small) {
                 if (pos < (unsigned)n) p.us[pos] = v;
                 else set_error(ctl, kErrNotConverged);
             }
-            if (d > kSmallDeg) list_changed(p, live, v, d);
+            if (d > p.tn.small_deg) list_changed(p, live, v, d);
         }
         if (!dom.sync()) return;
         if (threadIdx.x == 0) ++st[kStBarriers];
@@ -434,7 +437,7 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
             const int np = 1 - par;
             UpdateArc<Off> f{p.vinfo, p.oldcore, p.histo, p.tl[np], p.wl[np], p.bl[np],
                              ctl,     live,      np,      (unsigned)n};
-            expand(p.rp, p.ci, p.us, nus, p.ub, nub, gwarp, nwarps, f,
+            expand(p.rp, p.ci, p.us, nus, p.ub, nub, gwarp, nwarps, f, p.tn,
                    batch_width(nus, nub, nwarps));
             arcs += f.n_arcs;
             atomics += f.n_atomics;

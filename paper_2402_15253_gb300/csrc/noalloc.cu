@@ -35,8 +35,9 @@ namespace {
 // Largest graph this entry point accepts (see include/pico.h).
 constexpr long long kMaxN = PICO_NOALLOC_MAX_VERTICES;
 constexpr long long kMaxM = PICO_NOALLOC_MAX_ARCS;
-// Status record + PeelOne scratch for the limits above (16.4 MiB), rounded up.
-constexpr size_t kNoAllocScratchBytes = size_t(17) << 20;
+// Status record + PeelOne scratch for the limits above under every allowed
+// tuning (17.9 MiB), rounded up.
+constexpr size_t kNoAllocScratchBytes = size_t(19) << 20;
 constexpr size_t kStatusBytes = 512;   // LastResult header, padded to 256-byte alignment
 // The status record's header (status, statistics, trace switch) must fit in
 // kStatusBytes; its trace array is never written by this entry point.
@@ -87,6 +88,8 @@ int noalloc_device(NoAllocDevice **out)
         d.cfg.sms = sms;
         d.cfg.max_blocks_per_sm = 2;
         d.cfg.limit_ns = 4000ull * 1000000ull;
+        d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk};
+        d.cfg.batched_threads = pico::kThreads;
         d.ready = true;
     }
     *out = &d;

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 size_t chunk_capacity(long long m)
 {
-    return (size_t)(m / kChunk + m / (kSmallDeg + 1) + 2);
+    // enough for every allowed tuning (chunk >= kMinChunk, small_deg >= kMinSmallDeg)
+    return (size_t)(m / kMinChunk + m / (kMinSmallDeg + 1) + 2);
 }
 
 size_t peelone_ws_bytes(long long n, long long m)
@@ -66,6 +67,7 @@ int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *
     p.qs = c.take<int>(n);
     p.qb_cap = (unsigned)chunk_capacity(m);
     p.qb = c.take<int2>(p.qb_cap);
+    p.tn = cfg.tn;
     if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
 
     static int occ[64] = {};

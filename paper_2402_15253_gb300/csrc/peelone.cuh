@@ -47,6 +47,7 @@ struct Params {
     int2 *qb;             // queue of (vertex, chunk) entries of large vertices
     unsigned qb_cap;
     Ctrl *ctl;            // status word (errors)
+    Tuning tn;
 };
 
 template <typename Off>
@@ -61,6 +62,7 @@ struct Arc {
     unsigned *live;
     int k;
     unsigned qs_cap;
+    Tuning tn;
     unsigned long long n_arcs = 0, n_atomics = 0;
 
     __device__ __forceinline__ void item(int, int &, int &) {}
@@ -91,7 +93,7 @@ struct Arc {
             bool small = false, large = false;
             if (push) {
                 d = (long long)(rp[u[j] + 1] - rp[u[j]]);
-                small = d <= kSmallDeg;
+                small = d <= tn.small_deg;
                 large = !small;
             }
             const unsigned pos = warp_push(&live[L_QS], small);
@@ -99,7 +101,7 @@ struct Arc {
                 if (pos < qs_cap) qs[pos] = u[j];
                 else set_error(ctl, kErrNotConverged);
             }
-            warp_push_chunks(large, u[j], d, qb, &live[L_QB], qb_cap, ctl);
+            warp_push_chunks(large, u[j], d, qb, &live[L_QB], qb_cap, ctl, tn.chunk);
         }
     }
 };
@@ -190,7 +192,7 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
             for (int j = 0; j < kScanItems; ++j) {
                 d[j] = 0;
                 if (c[j] == k) d[j] = (long long)(p.rp[v[j] + 1] - p.rp[v[j]]);
-                nsmall += (c[j] == k && d[j] <= kSmallDeg);
+                nsmall += (c[j] == k && d[j] <= p.tn.small_deg);
                 nkeep += (c[j] > k);
                 if (c[j] > k) mx = max(mx, (unsigned)(INT_MAX - c[j]));
             }
@@ -198,7 +200,7 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
             block_alloc2(nsmall, nkeep, &live[L_QS], &live[L_KEPT + slot], pq, pk, s_tmp);
 #pragma unroll
             for (int j = 0; j < kScanItems; ++j) {
-                if (c[j] == k && d[j] <= kSmallDeg) {
+                if (c[j] == k && d[j] <= p.tn.small_deg) {
                     if (pq < (unsigned)n) p.qs[pq] = v[j];
                     else set_error(ctl, kErrNotConverged);
                     ++pq;
@@ -207,8 +209,8 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
             }
 #pragma unroll
             for (int j = 0; j < kScanItems; ++j)
-                warp_push_chunks(c[j] == k && d[j] > kSmallDeg, v[j], d[j], p.qb, &live[L_QB],
-                                 p.qb_cap, ctl);
+                warp_push_chunks(c[j] == k && d[j] > p.tn.small_deg, v[j], d[j], p.qb, &live[L_QB],
+                                 p.qb_cap, ctl, p.tn.chunk);
         }
         block_max_to(mx, &live[L_MIN + slot], s_tmp);
         if (!dom.sync()) return;
@@ -237,8 +239,8 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
         unsigned s0 = qs0, s1 = qb0;
         while (s0 < e0 || s1 < e1) {
             const unsigned units = (e0 - s0 + 31) / 32 + (e1 - s1);
-            Arc<Off> f{p.rp, p.core, p.qs, p.qb, p.qb_cap, ctl, live, k, (unsigned)n};
-            expand(p.rp, p.ci, p.qs + s0, e0 - s0, p.qb + s1, e1 - s1, gwarp, nwarps, f,
+            Arc<Off> f{p.rp, p.core, p.qs, p.qb, p.qb_cap, ctl, live, k, (unsigned)n, p.tn};
+            expand(p.rp, p.ci, p.qs + s0, e0 - s0, p.qb + s1, e1 - s1, gwarp, nwarps, f, p.tn,
                    batch_width(e0 - s0, e1 - s1, nwarps));
             arcs += f.n_arcs;
             atomics += f.n_atomics;

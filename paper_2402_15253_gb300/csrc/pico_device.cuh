@@ -11,9 +11,9 @@
 // * block_push2 / warp_push: aggregated appends to global lists (one atomic
 //   per block or per warp instead of one per element).
 // * expand: load-balanced traversal of the adjacency of a vertex list. Small
-//   vertices (degree <= kSmallDeg) are taken 32 at a time by a warp, which
+//   vertices (degree <= small_deg) are taken 32 at a time by a warp, which
 //   walks their concatenated neighbour lists with all lanes; large vertices
-//   are pre-split into chunks of kChunk arcs, one chunk per warp.
+//   are pre-split into chunks of `chunk` arcs, one chunk per warp.
 #pragma once
 
 #include <cstdint>
@@ -23,8 +23,19 @@
 namespace pico {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSmallDeg = 32;     // degree at or below which a vertex is "small"
-constexpr int kChunk = 256;       // arcs per chunk of a large vertex
+// Work assignment by degree class (tunable per device, see Tuning): a vertex
+// of degree <= small_deg is "small" (batched 32 per warp unit); a larger one
+// is split into chunks of `chunk` arcs, one chunk per warp unit. The scratch
+// bounds assume small_deg >= kMinSmallDeg and chunk >= kMinChunk.
+constexpr int kSmallDeg = 32;     // default small-degree threshold
+constexpr int kChunk = 256;       // default chunk size
+constexpr int kMinSmallDeg = 32, kMaxSmallDeg = 256;
+constexpr int kMinChunk = 64, kMaxChunk = 4096;
+
+struct Tuning {
+    int small_deg;
+    int chunk;
+};
 constexpr int kThreads = 512;     // threads per CTA of the persistent kernels
 constexpr int kLiveWords = 32;
 
@@ -316,11 +327,11 @@ __device__ __forceinline__ void block_min_to(int v, int *target, int *s)
 // ---------------------------------------------------------------------------
 // load-balanced adjacency expansion
 // ---------------------------------------------------------------------------
-// Appends the chunk entries of a large vertex (degree d > kSmallDeg).
+// Appends the chunk entries of a large vertex (degree d > small_deg).
 __device__ __forceinline__ bool push_chunks(int v, long long d, int2 *list, unsigned *counter,
-                                            unsigned cap)
+                                            unsigned cap, int chunk)
 {
-    const unsigned nch = (unsigned)((d + kChunk - 1) / kChunk);
+    const unsigned nch = (unsigned)((d + chunk - 1) / chunk);
     const unsigned pos = atomicAdd(counter, nch);
     if ((unsigned long long)pos + nch > cap) return false;
     for (unsigned c = 0; c < nch; ++c) list[pos + c] = make_int2(v, (int)c);
@@ -329,9 +340,10 @@ __device__ __forceinline__ bool push_chunks(int v, long long d, int2 *list, unsi
 
 // Warp-cooperative append of the chunk entries of large vertices: every
 // lane with `pred` owns vertex v of degree d; the whole warp writes the
-// ceil(d / kChunk) entries of each such vertex in turn.
+// ceil(d / chunk) entries of each such vertex in turn.
 __device__ __forceinline__ void warp_push_chunks(bool pred, int v, long long d, int2 *list,
-                                                 unsigned *counter, unsigned cap, Ctrl *ctl)
+                                                 unsigned *counter, unsigned cap, Ctrl *ctl,
+                                                 int chunk)
 {
     const int lane = threadIdx.x & 31;
     unsigned m = __ballot_sync(kFull, pred);
@@ -340,7 +352,7 @@ __device__ __forceinline__ void warp_push_chunks(bool pred, int v, long long d, 
         m &= m - 1;
         const int vv = __shfl_sync(kFull, v, src);
         const long long dd = __shfl_sync(kFull, d, src);
-        const unsigned nch = (unsigned)((dd + kChunk - 1) / kChunk);
+        const unsigned nch = (unsigned)((dd + chunk - 1) / chunk);
         unsigned pos = 0;
         if (lane == 0) pos = atomicAdd(counter, nch);
         pos = __shfl_sync(kFull, pos, 0);
@@ -371,7 +383,7 @@ __device__ __forceinline__ void red_add(int *p, int v)
 //                                        called by ALL 32 lanes together with
 //                                        U arcs (v -> u) per lane; rs = row_ptr[v]
 // `small` lists small vertices (nullptr: the identity list 0..nsmall-1, where
-// vertices with degree > kSmallDeg are skipped because their chunks are in
+// vertices with degree > tn.small_deg are skipped because their chunks are in
 // `big`). `big` lists (vertex, chunk) pairs.
 // Small vertices per warp unit for a phase with nsmall small vertices and
 // nbig chunk units: 32 when there is enough work for every warp, otherwise
@@ -390,7 +402,7 @@ template <typename Off, typename F>
 __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__restrict__ ci,
                                        const int *small, unsigned nsmall, const int2 *big,
                                        unsigned nbig, unsigned gwarp, unsigned nwarps, F &f,
-                                       unsigned vb = 32u)
+                                       const Tuning &tn, unsigned vb = 32u)
 {
     constexpr int U = F::kArcs;
     const int lane = threadIdx.x & 31;
@@ -405,7 +417,7 @@ __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__
                 v = small ? ldcg(small + idx) : (int)idx;
                 rs = rp[v];
                 const Off dd = rp[v + 1] - rs;
-                if (dd <= kSmallDeg) {
+                if (dd <= tn.small_deg) {
                     d = (int)dd;
                     if (d > 0) f.item(v, a, b);
                 }
@@ -445,8 +457,8 @@ __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__
             const int2 ent = __ldcg(big + (unit - nbatch));   // written by other CTAs
             const int v = ent.x;
             const Off rs = rp[v], re = rp[v + 1];
-            const Off s = rs + (Off)ent.y * kChunk;
-            const Off t = (s + kChunk < re) ? s + kChunk : re;
+            const Off s = rs + (Off)ent.y * tn.chunk;
+            const Off t = (s + tn.chunk < re) ? s + tn.chunk : re;
             int a = 0, b = 0;
             f.item(v, a, b);
             for (Off e0 = s; e0 < t; e0 += 32 * U) {

@@ -6,16 +6,20 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "pico_device.cuh"
+
 namespace pico {
 
 struct LastResult;
 
-// Launch geometry of the persistent kernels for the current device.
+// Launch geometry and tuning of the persistent kernels for the current device.
 struct LaunchCfg {
     int device;
     int sms;                       // streaming multiprocessors
     int max_blocks_per_sm;         // cap on co-resident CTAs per SM
     unsigned long long limit_ns;   // time limit of every device-side wait
+    Tuning tn;                     // degree-class work assignment
+    int batched_threads;           // threads per CTA of the batched kernel (256 or 512)
 };
 
 // Sub-buffer carving of a scratch allocation (256-byte aligned pieces).
