@@ -208,11 +208,17 @@ def bench_batched(pico, dev, stream, G: int, reps: int = 5):
     pico.pico_set_tuning(*autotune.DEFAULT)
     best_peel, timings = autotune.tune_batched(pico, pb.vtx_off, pb.arc_off, pb.row_ptr, pb.col_idx,
                                                "peelone", reps=2, use_cache=False)
-    tuned = {"peelone": best_peel, "histocore": autotune.DEFAULT}
+    # HistoCore's batch is ~10x slower: only its CTA size and cluster threshold are tuned
+    best_histo, _ = autotune.tune_batched(pico, pb.vtx_off, pb.arc_off, pb.row_ptr, pb.col_idx,
+                                          "histocore", reps=1, use_cache=False,
+                                          cands=[autotune.override(autotune.DEFAULT, o)
+                                                 for o in autotune.stages(True)[1]])
+    tuned = {"peelone": best_peel, "histocore": best_histo}
     res = {"workload": f"{G} graphs, log-uniform 100..200,000 vertices, half ER (mean degree "
                        f"4-64), half R-MAT (edge factor 8-32); {tv} vertices, {ta} arcs",
            "graphs": G, "vertices": tv, "arcs": ta}
-    res["tuning"] = {a: {"small_deg": t[0], "chunk": t[1], "cta_threads": t[2]}
+    res["tuning"] = {a: {"small_deg": t[0], "chunk": t[1], "cta_threads": t[2],
+                         "cluster_min_arcs": (1 << t[3]) if t[3] < 62 else None}
                      for a, t in tuned.items()}
     res["peelone_default_tuning_ms"] = timings[autotune.DEFAULT]
     for algo in ("peelone", "histocore"):
@@ -276,6 +282,11 @@ def bench_batched(pico, dev, stream, G: int, reps: int = 5):
     res["speedup_vs_one_launch_per_graph"] = ms_single / res["peelone"]["ms"]
     res["speedup_graph_replay_vs_one_launch_per_graph"] = ms_single / ms_graph
     return res
+
+
+def autotune_default():
+    from paper_2402_15253_gb300 import autotune
+    return autotune.DEFAULT
 
 
 def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int = 256,
@@ -343,6 +354,7 @@ def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int
         return {"graphs_per_s": requests / span, "p50_ms": float(lat.quantile(0.5)),
                 "p99_ms": float(lat.quantile(0.99)), "mean_ms": float(lat.mean())}
 
+    pico.pico_set_tuning(*autotune_default())
     capacity = run(None, False)["graphs_per_s"]
     res = {"workload": f"{requests} requests, Poisson arrivals, pool of {pool_size} graphs "
                        f"(log-uniform 100..200,000 vertices, half ER, half R-MAT; "

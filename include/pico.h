@@ -253,12 +253,14 @@ int pico_selftest_wait_timeout(int limit_ms, pico_stream_t stream);
  * autotuner, paper_2402_15253_gb300/autotune.py): vertices of degree at most
  * small_deg (32..256) are batched 32 per warp; larger ones are split into
  * chunks of `chunk` arcs (64..4096), one per warp; batched_threads (256 or
- * 512) is the CTA size of the batched kernel (one CTA per graph). Applies to
- * later calls on the device; defaults 32, 256, 512. Results never depend on
- * these values, only the speed does.
+ * 512) is the CTA size of the batched kernel, where a graph with at least
+ * 2^cluster_log2 arcs (10..62; 62 disables clusters) is solved by a cluster of
+ * 8 CTAs and every other graph by one CTA. Applies to later calls on the
+ * device; defaults 32, 256, 512, 21. Results never depend on these values,
+ * only the speed does.
  */
-int pico_set_tuning(int small_deg, int chunk, int batched_threads);
-int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads);
+int pico_set_tuning(int small_deg, int chunk, int batched_threads, int cluster_log2);
+int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads, int *cluster_log2);
 
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int pico_version(void);

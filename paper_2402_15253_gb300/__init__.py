@@ -104,9 +104,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_server_destroy.restype = i32
     L.pico_clock_ns.argtypes = []
     L.pico_clock_ns.restype = i64
-    L.pico_set_tuning.argtypes = [i32, i32, i32]
+    L.pico_set_tuning.argtypes = [i32, i32, i32, i32]
     L.pico_set_tuning.restype = i32
-    L.pico_get_tuning.argtypes = [vp, vp, vp]
+    L.pico_get_tuning.argtypes = [vp, vp, vp, vp]
     L.pico_get_tuning.restype = i32
     L.pico_selftest_wait_timeout.argtypes = [i32, vp]
     L.pico_selftest_wait_timeout.restype = i32
@@ -232,16 +232,16 @@ def pico_get_trace(stream=None, cap: int = 8192) -> list:
     return [(PHASES[kind], units, ns / 1e6) for kind, units, ns in b]
 
 
-def pico_set_tuning(small_deg: int, chunk: int, batched_threads: int) -> int:
-    return load().pico_set_tuning(small_deg, chunk, batched_threads)
+def pico_set_tuning(small_deg: int, chunk: int, batched_threads: int, cluster_log2: int = 21) -> int:
+    return load().pico_set_tuning(small_deg, chunk, batched_threads, cluster_log2)
 
 
 def pico_get_tuning() -> tuple:
-    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    rc = load().pico_get_tuning(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = load().pico_get_tuning(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
     if rc != PICO_OK:
         raise PicoError(rc, "pico_get_tuning")
-    return a.value, b.value, c.value
+    return a.value, b.value, c.value, d.value
 
 
 def pico_selftest_wait_timeout(limit_ms: int, stream=None) -> int:

@@ -2,13 +2,15 @@
 
 The kernels assign work by degree class: vertices of degree <= small_deg are
 batched 32 per warp, larger ones are split into chunks of `chunk` arcs (one
-per warp), and the batched kernel gives each graph one CTA of
-`batched_threads` threads. The best values depend on the graph mix and the
-GPU; results never do. This module times candidate settings on the caller's
-own workload (CUDA events on the call's stream, median of several runs after a
-warm-up), keeps the fastest, applies it with pico_set_tuning, and caches it in
-a JSON file keyed by GPU name, method, call kind and power-of-two size
-classes, so later runs of a similar workload start tuned.
+per warp); the batched kernel gives each graph one CTA of `batched_threads`
+threads, or a cluster of 8 CTAs when it has at least 2^cluster_log2 arcs. The
+best values depend on the graph mix and the GPU; results never do. This
+module times candidate settings on the caller's own workload (CUDA events on
+the call's stream, median of several runs after a warm-up) in two stages -
+first the degree classes, then the CTA size and cluster threshold - keeps the
+fastest, applies it with pico_set_tuning, and caches it in a JSON file keyed
+by GPU name, method, call kind and power-of-two size classes, so later runs
+of a similar workload start tuned.
 
 Cache file: $PICO_TUNING_CACHE, else ~/.cache/pico_gb300/tuning.json.
 """
@@ -24,18 +26,41 @@ from typing import Callable, Iterable, Sequence
 SMALL_DEG = (32, 64, 128)
 CHUNK = (128, 256, 1024)
 THREADS = (256, 512)
-DEFAULT = (32, 256, 512)
+CLUSTER = (21, 23, 62)          # 62: no clusters
+DEFAULT = (32, 256, 512, 21)
 
 
-def candidates(batched: bool) -> list[tuple[int, int, int]]:
-    """The grid of settings tried: small_deg x chunk (x CTA size when batched)."""
-    threads = THREADS if batched else (DEFAULT[2],)
-    return [(s, c, t) for s in SMALL_DEG for c in CHUNK for t in threads]
+def stages(batched: bool) -> list[list[dict]]:
+    """The search: stage 1 varies small_deg x chunk; stage 2 (batched only)
+    varies CTA size x cluster threshold around the best of stage 1."""
+    s1 = [{"small_deg": s, "chunk": c} for s in SMALL_DEG for c in CHUNK]
+    if not batched:
+        return [s1]
+    s2 = [{"threads": t, "cluster_log2": k} for t in THREADS for k in CLUSTER]
+    return [s1, s2]
+
+
+def candidates(batched: bool) -> list[tuple[int, int, int, int]]:
+    """Every setting the staged search can reach (for tests)."""
+    out = [override(DEFAULT, o) for st in stages(batched) for o in st]
+    return list(dict.fromkeys(out))
+
+
+_FIELDS = ("small_deg", "chunk", "threads", "cluster_log2")
+
+
+def override(cand: Sequence[int], changes: dict) -> tuple:
+    c = list(cand)
+    for k, v in changes.items():
+        c[_FIELDS.index(k)] = v
+    return tuple(c)
 
 
 def valid(cand: Sequence[int]) -> bool:
-    s, c, t = cand
-    return 32 <= s <= 256 and 64 <= c <= 4096 and t in (256, 512)
+    if len(cand) != 4:
+        return False
+    s, c, t, k = cand
+    return 32 <= s <= 256 and 64 <= c <= 4096 and t in (256, 512) and 10 <= k <= 62
 
 
 def size_class(x: int) -> int:
@@ -91,6 +116,18 @@ def tune(run: Callable[[tuple], float], cands: Iterable[tuple], reps: int = 3) -
     return pick(timings), timings
 
 
+def tune_staged(run: Callable[[tuple], float], stage_list, start=DEFAULT, reps: int = 3):
+    """Coordinate search: each stage tries its overrides on the best setting
+    so far. Returns (best, {cand: ms} over all stages)."""
+    best, timings = tuple(start), {}
+    for st in stage_list:
+        cands = list(dict.fromkeys(override(best, o) for o in st))
+        b, t = tune(run, cands, reps)
+        timings.update(t)
+        best = b
+    return best, timings
+
+
 def _timer(pico, stream, call):
     import torch
 
@@ -129,7 +166,8 @@ def tune_batched(pico, vtx_off, arc_off, row_ptr, col_idx, algo="peelone", cands
         if rc != pico.PICO_OK:
             raise pico.PicoError(rc, "batched")
 
-    best, timings = tune(_timer(pico, stream, call), cands or candidates(True), reps)
+    run = _timer(pico, stream, call)
+    best, timings = tune(run, cands, reps) if cands else tune_staged(run, stages(True), reps=reps)
     pico.pico_set_tuning(*best)
     if use_cache:
         key = cache_key(torch.cuda.get_device_name(), algo, "batched", tv, ta, G)
@@ -153,7 +191,8 @@ def tune_single(pico, row_ptr, col_idx, algo="peelone", cands=None, reps: int = 
         if rc != pico.PICO_OK:
             raise pico.PicoError(rc, "coreness")
 
-    best, timings = tune(_timer(pico, stream, call), cands or candidates(False), reps)
+    run = _timer(pico, stream, call)
+    best, timings = tune(run, cands, reps) if cands else tune_staged(run, stages(False), reps=reps)
     pico.pico_set_tuning(*best)
     if use_cache:
         key = cache_key(torch.cuda.get_device_name(), algo, "single", n, m)

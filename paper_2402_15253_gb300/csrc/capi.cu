@@ -53,7 +53,7 @@ int device_state(DeviceState **out)
         d.cfg.sms = prop.multiProcessorCount;
         d.cfg.max_blocks_per_sm = (int)env_ll("PICO_BLOCKS_PER_SM", 2);
         d.cfg.limit_ns = (unsigned long long)env_ll("PICO_WAIT_LIMIT_MS", 4000) * 1000000ull;
-        d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk};
+        d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk, pico::kClusterLog2};
         d.cfg.batched_threads = pico::kThreads;
         if (cudaMalloc(&d.last, sizeof(pico::LastResult)) != cudaSuccess) {
             cudaGetLastError();
@@ -313,24 +313,25 @@ int pico_selftest_wait_timeout(int limit_ms, pico_stream_t stream)
     return pico_last_device_status(stream);
 }
 
-int pico_set_tuning(int small_deg, int chunk, int batched_threads)
+int pico_set_tuning(int small_deg, int chunk, int batched_threads, int cluster_log2)
 {
     if (small_deg < pico::kMinSmallDeg || small_deg > pico::kMaxSmallDeg ||
         chunk < pico::kMinChunk || chunk > pico::kMaxChunk ||
-        (batched_threads != 256 && batched_threads != 512))
+        (batched_threads != 256 && batched_threads != 512) || cluster_log2 < 10 ||
+        cluster_log2 > pico::kClusterNever)
         return PICO_ERR_INVALID_ARG;
     DeviceState *d = nullptr;
     int rc = device_state(&d);
     if (rc != PICO_OK) return rc;
     std::lock_guard<std::mutex> lock(g_mu);
-    d->cfg.tn = pico::Tuning{small_deg, chunk};
+    d->cfg.tn = pico::Tuning{small_deg, chunk, cluster_log2};
     d->cfg.batched_threads = batched_threads;
     return PICO_OK;
 }
 
-int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads)
+int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads, int *cluster_log2)
 {
-    if (!small_deg || !chunk || !batched_threads) return PICO_ERR_INVALID_ARG;
+    if (!small_deg || !chunk || !batched_threads || !cluster_log2) return PICO_ERR_INVALID_ARG;
     DeviceState *d = nullptr;
     int rc = device_state(&d);
     if (rc != PICO_OK) return rc;
@@ -338,6 +339,7 @@ int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads)
     *small_deg = d->cfg.tn.small_deg;
     *chunk = d->cfg.tn.chunk;
     *batched_threads = d->cfg.batched_threads;
+    *cluster_log2 = d->cfg.tn.cluster_log2;
     return PICO_OK;
 }
 

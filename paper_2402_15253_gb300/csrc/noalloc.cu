@@ -88,7 +88,7 @@ int noalloc_device(NoAllocDevice **out)
         d.cfg.sms = sms;
         d.cfg.max_blocks_per_sm = 2;
         d.cfg.limit_ns = 4000ull * 1000000ull;
-        d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk};
+        d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk, pico::kClusterLog2};
         d.cfg.batched_threads = pico::kThreads;
         d.ready = true;
     }

@@ -35,7 +35,10 @@ constexpr int kMinChunk = 64, kMaxChunk = 4096;
 struct Tuning {
     int small_deg;
     int chunk;
+    int cluster_log2;   // batched form: graphs with >= 2^cluster_log2 arcs use a cluster
 };
+constexpr int kClusterNever = 62;   // cluster_log2 value that disables clusters
+constexpr int kClusterLog2 = 21;    // default
 constexpr int kThreads = 512;     // threads per CTA of the persistent kernels
 constexpr int kLiveWords = 32;
 
@@ -703,6 +706,54 @@ struct CtaDom {
     __device__ __forceinline__ unsigned cta() const { return 0; }
     __device__ __forceinline__ unsigned ncta() const { return 1; }
     __device__ __forceinline__ bool leader() const { return threadIdx.x == 0; }
+};
+
+}  // namespace pico
+
+#include <cooperative_groups.h>
+
+namespace pico {
+
+// ClusterDom: the CTAs of one thread-block cluster work on one graph (the
+// batched form's large graphs). The counters live in the shared memory of
+// the cluster's rank-0 CTA and are reached by every CTA through distributed
+// shared memory; a phase ends with the hardware cluster barrier, after which
+// each CTA copies the counters into its own snapshot and a second cluster
+// barrier keeps them unchanged until every CTA has copied them. The global
+// status is read by rank 0 alone into counter word kClusterStatusWord, so
+// every CTA takes the same decision after the same barrier (a CTA leaving
+// alone would leave the others waiting at the next cluster barrier).
+constexpr int kClusterStatusWord = kLiveWords - 1;
+
+struct ClusterDom {
+    Ctrl *ctl;
+    unsigned *s_live;   // this CTA's counter words (only rank 0's are used)
+    unsigned *live0;    // rank 0's counter words (distributed shared memory)
+    unsigned *s_snap;   // kLiveWords + 1 words, this CTA's shared memory
+    unsigned rank, size;
+    unsigned nsync;
+    static constexpr bool kGrid = false;
+    __device__ __forceinline__ void reset()
+    {
+        cooperative_groups::this_cluster().sync();
+        if (rank == 0 && threadIdx.x < kLiveWords) s_live[threadIdx.x] = 0;
+        cooperative_groups::this_cluster().sync();
+    }
+    __device__ __forceinline__ unsigned *live() const { return live0; }
+    __device__ __forceinline__ bool sync()
+    {
+        if (rank == 0 && threadIdx.x == 0 && (++nsync & 255u) == 0)
+            s_live[kClusterStatusWord] = (unsigned)status_of(ctl);
+        cooperative_groups::this_cluster().sync();
+        if (threadIdx.x < kLiveWords) s_snap[threadIdx.x] = live0[threadIdx.x];
+        cooperative_groups::this_cluster().sync();
+        return s_snap[kClusterStatusWord] == 0;
+    }
+    __device__ __forceinline__ unsigned tid() const { return rank * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ unsigned nthreads() const { return size * blockDim.x; }
+    __device__ __forceinline__ unsigned cta() const { return rank; }
+    __device__ __forceinline__ unsigned ncta() const { return size; }
+    __device__ __forceinline__ bool leader() const { return rank == 0 && threadIdx.x == 0; }
 };
 
 }  // namespace pico

@@ -114,3 +114,18 @@ def test_full_size_batch_sampled(pico):
         sub = pb.graph(int(g))
         want = oracle.bz_coreness(sub.row_ptr.cpu().numpy(), sub.col_idx.cpu().numpy())
         assert np.array_equal(got[vo[g]:vo[g + 1]], want), f"graph {g}"
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_large_graphs_solved_by_clusters(pico, algo):
+    """Graphs with at least 2^21 arcs are solved by a thread-block cluster;
+    mixed with small ones, every result must still be the oracle's."""
+    graphs = [gg.rmat_graph(17, 16, 61),          # ~3.8 M arcs
+              gg.complete_graph(1600),            # 2.56 M arcs, HistoCore CTA walks
+              gg.spec_graph(gg.batch_specs(1, 62)[0]),
+              gg.grid_graph(800, 800),            # 2.56 M arcs, long peel
+              gg.rmat_graph(12, 8, 63)]
+    assert sum(g.arcs >= (1 << 21) for g in graphs) == 3
+    pb = gg.pack_graphs(graphs)
+    got = run_batch(pico, pb, algo)
+    assert np.array_equal(got, oracle_batch(pb))
