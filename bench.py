@@ -373,6 +373,27 @@ def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int
     return res
 
 
+BYTES_MODEL = {
+    "peelone": "B_PeelOne = B_min + 4 B per decrement + 4 B per residual entry scanned, "
+               "B_min = w_r(n+1) + 8 B/arc + 4 B/vertex",
+    "histocore": "B_HistoCore = B_min + 4(A+n) (histogram build) + 4 B per SumHisto slot "
+                 "+ 8 B per arc scanned by UpdateHisto + 8 B per neighbour updated",
+}
+
+
+def method_bytes(algo: str, st: dict, n: int, arcs: int, w_r: int) -> int:
+    """Algorithmic bytes of one launch (the per-graph figures of the
+    measurement plan), from the launch's own counters."""
+    b_min = w_r * (n + 1) + 8 * arcs + 4 * n
+    if algo == "peelone":
+        return b_min + 4 * st["atomics"] + 4 * st["scanned"]
+    # HistoCore: InitHisto scans every arc once (counted in st["arcs"] too);
+    # each updated neighbour costs two slot edits (counted in st["atomics"])
+    update_arcs = st["arcs"] - arcs
+    updated = max(0, (st["atomics"] - arcs) // 2)
+    return b_min + 4 * (arcs + n) + 4 * st["slots"] + 8 * update_arcs + 8 * updated
+
+
 def job_totals(local_ms: float, local_units: int, device=None):
     """Whole-job time and work over the ranks of the current process group
     (or this process alone): the slowest rank's time and the sum of the
@@ -540,14 +561,18 @@ def main():
     total_ms, units = job_totals(sum(step_ms), 2 * m_und * args.steps, dev)
     value = units / (total_ms / 1000.0)
 
-    # roofline of the dominant kernel: algorithm-neutral bytes B_min per launch
+    # roofline of the dominant kernel against its method's algorithmic bytes
     b_min = w_r * (n + 1) + 4 * arcs + 4 * arcs + 4 * n
+    b_alg = {a: method_bytes(a, stats[a], n, arcs, w_r) for a in stats}
     peak, peak_kind = peaks()
     mean_ms = {a: statistics.mean(v) for a, v in per.items()}
     dom = max(mean_ms, key=mean_ms.get)
-    achieved = b_min / (mean_ms[dom] / 1000.0) / 1e9
+    achieved = b_alg[dom] / (mean_ms[dom] / 1000.0) / 1e9
     traffic, traffic_src = recorded_traffic(args.workload, dom, arcs)
     methods = {a: {"ms_mean": mean_ms[a], "ms_median": statistics.median(per[a]),
+                   "alg_bytes": b_alg[a],
+                   "alg_gbs": b_alg[a] / (mean_ms[a] / 1000.0) / 1e9,
+                   "alg_frac_of_" + peak_kind: b_alg[a] / (mean_ms[a] / 1000.0) / 1e9 / peak,
                    "edges_per_s": m_und / (mean_ms[a] / 1000.0),
                    "bmin_gbs": b_min / (mean_ms[a] / 1000.0) / 1e9,
                    "bmin_frac_of_" + peak_kind: b_min / (mean_ms[a] / 1000.0) / 1e9 / peak,
@@ -567,8 +592,10 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "traffic_source": traffic_src,
-                     "bytes_per_launch": b_min, "peak_kind": peak_kind,
-                     "bytes_model": "B_min = w_r(n+1) + 8 B/arc + 4 B/vertex"},
+                     "bytes_per_launch": b_alg[dom], "peak_kind": peak_kind,
+                     "bytes_model": BYTES_MODEL[dom],
+                     "bmin_bytes": b_min,
+                     "bmin_frac": b_min / (mean_ms[dom] / 1000.0) / 1e9 / peak},
         "tuning": {a: {"small_deg": t[0], "chunk": t[1]} for a, t in tuned.items()},
         "methods": methods,
         "gpu_launches": 2 * args.steps,

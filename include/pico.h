@@ -214,6 +214,7 @@ typedef struct {
     int64_t atomics;     /* atomic read-modify-writes on core[] or histo[] */
     int64_t slots;       /* HistoCore: histogram slots read by SumHisto */
     int64_t blocks;      /* CTAs of the persistent launch */
+    int64_t scanned;     /* PeelOne: residual-list entries read, summed over scans */
     /* Device time (ns) and count per phase kind, measured by CTA 0 from one
        grid barrier to the next: [0] init, [1] PeelOne residual scan,
        [2..4] PeelOne frontier waves with < 64 work units / fewer units than

@@ -48,7 +48,7 @@ PHASES = ("init", "scan", "wave_tiny", "wave_mid", "wave_wide", "inithisto", "su
 class pico_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "algo", "levels", "kmax", "subrounds", "scans", "rounds", "frontier", "barriers",
-        "arcs", "atomics", "slots", "blocks")] + [("phase_ns", ctypes.c_int64 * 8),
+        "arcs", "atomics", "slots", "blocks", "scanned")] + [("phase_ns", ctypes.c_int64 * 8),
                                                   ("phase_count", ctypes.c_int64 * 8)]
 
     def as_dict(self) -> dict:

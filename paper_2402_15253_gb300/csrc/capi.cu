@@ -260,6 +260,7 @@ int pico_get_stats(pico_stream_t stream, pico_stats *out)
     out->atomics = (int64_t)h.stats[pico::kStAtomics];
     out->slots = (int64_t)h.stats[pico::kStSlots];
     out->blocks = (int64_t)h.stats[pico::kStBlocks];
+    out->scanned = (int64_t)h.stats[pico::kStScanned];
     for (int i = 0; i < 8; ++i) {
         out->phase_ns[i] = (int64_t)h.stats[pico::kStPhaseNs + i];
         out->phase_count[i] = (int64_t)h.stats[pico::kStPhaseCount + i];

@@ -217,6 +217,7 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
         if (threadIdx.x == 0) {
             ++st[kStBarriers];
             ++st[kStScans];
+            st[kStScanned] += nres;
         }
         if (Dom::kGrid) clk.end(st, kPhScan, nres);
 

@@ -56,7 +56,7 @@ struct alignas(128) Line {
 // Statistics slots (match pico_stats field order after `algo`).
 enum StatIdx : int {
     kStLevels = 0, kStKmax, kStSubrounds, kStScans, kStRounds, kStFrontier,
-    kStBarriers, kStArcs, kStAtomics, kStSlots, kStBlocks,
+    kStBarriers, kStArcs, kStAtomics, kStSlots, kStBlocks, kStScanned,
     kStPhaseNs = 16,      // 16..23: device time per phase kind (CTA 0's view)
     kStPhaseCount = 24,   // 24..31: phases per kind
     kStCount = 32
