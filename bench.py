@@ -465,6 +465,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--tuning", default="auto",
+                    help="'auto' (autotune each method on the graph) or S,C,T,K: small_deg, "
+                         "chunk, batched CTA threads, cluster log2 arcs, for both methods")
     ap.add_argument("--serve-requests", type=int, default=0,
                     help="requests of the served-form measurement (0: skip)")
     args = ap.parse_args()
@@ -504,7 +507,12 @@ def main():
     from paper_2402_15253_gb300 import autotune
     tuned = {}
     for a in ("peelone", "histocore"):
-        tuned[a], _ = autotune.tune_single(pico, rp, ci, a, reps=2, use_cache=False)
+        if args.tuning == "auto":
+            tuned[a], _ = autotune.tune_single(pico, rp, ci, a, reps=2, use_cache=False)
+        else:
+            tuned[a] = tuple(int(x) for x in args.tuning.split(","))
+            if not autotune.valid(tuned[a]):
+                raise SystemExit(f"invalid --tuning {args.tuning}")
 
     def step(ev=None):
         for i, a in enumerate(("peelone", "histocore")):

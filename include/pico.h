@@ -210,11 +210,15 @@ typedef struct {
     int64_t rounds;      /* HistoCore: SumHisto/UpdateHisto rounds */
     int64_t frontier;    /* HistoCore: sum over rounds of |V_cnt| */
     int64_t barriers;    /* grid-wide barriers executed */
-    int64_t arcs;        /* adjacency entries read by the expansion phases */
+    int64_t arcs;        /* PeelOne: adjacency entries read by the expansion phases;
+                            HistoCore: arcs of InitHisto plus, per round, the arcs of the
+                            changed vertices (what Alg. 6 scans, in either direction) */
     int64_t atomics;     /* atomic read-modify-writes on core[] or histo[] */
     int64_t slots;       /* HistoCore: histogram slots read by SumHisto */
     int64_t blocks;      /* CTAs of the persistent launch */
     int64_t scanned;     /* PeelOne: residual-list entries read, summed over scans */
+    int64_t pulled;      /* HistoCore: arcs scanned by pull rounds of UpdateHisto */
+    int64_t pull_rounds; /* HistoCore: rounds whose UpdateHisto pulled */
     /* Device time (ns) and count per phase kind, measured by CTA 0 from one
        grid barrier to the next: [0] init, [1] PeelOne residual scan,
        [2..4] PeelOne frontier waves with < 64 work units / fewer units than
@@ -262,6 +266,26 @@ int pico_selftest_wait_timeout(int limit_ms, pico_stream_t stream);
  */
 int pico_set_tuning(int small_deg, int chunk, int batched_threads, int cluster_log2);
 int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads, int *cluster_log2);
+
+/* Direction of HistoCore's UpdateHisto (Sec. IV-B, Alg. 6). */
+#define PICO_UPDATE_AUTO 0   /* per round: pull when the round's changed vertices hold at
+                                least pull_pct % of the arcs of a graph with >= 2^22 arcs */
+#define PICO_UPDATE_PUSH 1   /* always push from the changed vertices (the paper's form) */
+#define PICO_UPDATE_PULL 2   /* always pull (every round, every graph size) */
+
+/*
+ * Sets the UpdateHisto direction of later HistoCore calls on the current
+ * device (no counterpart in the paper, which pushes). Pushing, each changed
+ * vertex edits the histogram rows of its neighbours; pulling, every vertex
+ * whose estimate an edit can reach walks its own adjacency and applies the
+ * edits of its changed neighbours to its own row. Both apply the same edits
+ * and give the same results and rounds; pulling scans more arcs but edits
+ * one row at a time, which keeps the edits in L2 when the rows a round
+ * touches exceed it. mode: PICO_UPDATE_*; pull_pct: 1..100, the auto-mode
+ * threshold (default 40). Returns PICO_ERR_INVALID_ARG for other values.
+ */
+int pico_set_histo_update(int mode, int pull_pct);
+int pico_get_histo_update(int *mode, int *pull_pct);
 
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int pico_version(void);

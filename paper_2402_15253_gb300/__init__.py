@@ -24,6 +24,11 @@ PICO_ALGO_PEELONE = 0
 PICO_ALGO_HISTOCORE = 1
 ALGOS = {"peelone": PICO_ALGO_PEELONE, "histocore": PICO_ALGO_HISTOCORE}
 
+PICO_UPDATE_AUTO = 0
+PICO_UPDATE_PUSH = 1
+PICO_UPDATE_PULL = 2
+UPDATES = {"auto": PICO_UPDATE_AUTO, "push": PICO_UPDATE_PUSH, "pull": PICO_UPDATE_PULL}
+
 PICO_OK = 0
 PICO_ERR_INVALID_ARG = -1
 PICO_ERR_OOM = -2
@@ -43,12 +48,15 @@ class PicoError(RuntimeError):
 
 PHASES = ("init", "scan", "wave_tiny", "wave_mid", "wave_wide", "inithisto", "sumhisto",
           "updatehisto")
+# trace-only kinds (counted under "updatehisto" in pico_stats.phase_ns)
+TRACE_KINDS = PHASES + ("updatehisto_pull",)
 
 
 class pico_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "algo", "levels", "kmax", "subrounds", "scans", "rounds", "frontier", "barriers",
-        "arcs", "atomics", "slots", "blocks", "scanned")] + [("phase_ns", ctypes.c_int64 * 8),
+        "arcs", "atomics", "slots", "blocks", "scanned", "pulled", "pull_rounds")] + [
+            ("phase_ns", ctypes.c_int64 * 8),
                                                   ("phase_count", ctypes.c_int64 * 8)]
 
     def as_dict(self) -> dict:
@@ -108,6 +116,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_set_tuning.restype = i32
     L.pico_get_tuning.argtypes = [vp, vp, vp, vp]
     L.pico_get_tuning.restype = i32
+    L.pico_set_histo_update.argtypes = [i32, i32]
+    L.pico_set_histo_update.restype = i32
+    L.pico_get_histo_update.argtypes = [vp, vp]
+    L.pico_get_histo_update.restype = i32
     L.pico_selftest_wait_timeout.argtypes = [i32, vp]
     L.pico_selftest_wait_timeout.restype = i32
     L.pico_get_trace.argtypes = [vp, vp, i32]
@@ -229,7 +241,22 @@ def pico_get_trace(stream=None, cap: int = 8192) -> list:
     if k < 0:
         raise PicoError(k, "pico_get_trace")
     b = buf[:3 * k].view(-1, 3).tolist()
-    return [(PHASES[kind], units, ns / 1e6) for kind, units, ns in b]
+    return [(TRACE_KINDS[kind], units, ns / 1e6) for kind, units, ns in b]
+
+
+PULL_PCT_DEFAULT = 40
+
+
+def pico_set_histo_update(mode: int, pull_pct: int = PULL_PCT_DEFAULT) -> int:
+    return load().pico_set_histo_update(mode, pull_pct)
+
+
+def pico_get_histo_update() -> tuple:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    rc = load().pico_get_histo_update(ctypes.byref(a), ctypes.byref(b))
+    if rc != PICO_OK:
+        raise PicoError(rc, "pico_get_histo_update")
+    return a.value, b.value
 
 
 def pico_set_tuning(small_deg: int, chunk: int, batched_threads: int, cluster_log2: int = 21) -> int:

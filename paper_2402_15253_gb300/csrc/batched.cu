@@ -38,8 +38,8 @@ struct BatchParams {
     int *core;
     int *order;
     int *res0, *res1, *qs;                          // PeelOne
-    int *oldcore, *histo, *lists[6], *us;           // HistoCore
-    int2 *vinfo;
+    int *histo, *lists[6], *us;                     // HistoCore
+    int2 *vinfo, *mv[2], *ichunks;
     int2 *chunks;                                   // both
     Ctrl *ctl;
     Tuning tn;
@@ -83,7 +83,7 @@ template <int Algo, typename Dom>
 __device__ __forceinline__ void solve_graph(const BatchParams &bp, int g, Dom &dom, unsigned *s_tmp,
                                             unsigned long long *st, PhaseClock &clk,
                                             unsigned long long &arcs, unsigned long long &atomics,
-                                            unsigned long long &slots)
+                                            unsigned long long &slots, unsigned long long &pulled)
 {
     const long long v0 = bp.vtx_off[g], n = bp.vtx_off[g + 1] - v0;
     const long long a0 = bp.arc_off[g], m = bp.arc_off[g + 1] - a0;
@@ -104,7 +104,8 @@ __device__ __forceinline__ void solve_graph(const BatchParams &bp, int g, Dom &d
         p.m = m;
         p.core = bp.core + v0;
         p.vinfo = bp.vinfo + v0;
-        p.oldcore = bp.oldcore + v0;
+        p.mv[0] = bp.mv[0] + v0;
+        p.mv[1] = bp.mv[1] + v0;
         p.histo = bp.histo + a0;
         p.tl[0] = bp.lists[0] + v0;
         p.wl[0] = bp.lists[1] + v0;
@@ -114,11 +115,12 @@ __device__ __forceinline__ void solve_graph(const BatchParams &bp, int g, Dom &d
         p.bl[1] = bp.lists[5] + v0;
         p.us = bp.us + v0;
         p.ub = chunks;
+        p.ib = bp.ichunks + (a0 / 16 + 2ll * g);
         p.ub_cap = chunk_cap;
         p.ctl = bp.ctl;
         p.zero_histo = true;
         p.tn = bp.tn;
-        histo::run(p, dom, s_tmp, st, clk, arcs, atomics, slots);
+        histo::run(p, dom, s_tmp, st, clk, arcs, atomics, slots, pulled);
     }
 }
 
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(Threads, 512 / Threads * 2)
     batched_kernel(BatchParams bp, LastResult *last)
 {
     namespace cg = cooperative_groups;
-    __shared__ unsigned s_live[kLiveWords];
+    __shared__ __align__(16) unsigned s_live[kLiveWords];   // 64-bit counters need 8-byte alignment
     __shared__ unsigned s_snap[kLiveWords + 1];
     __shared__ unsigned s_tmp[256];
     __shared__ unsigned long long s_red[32];
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(Threads, 512 / Threads * 2)
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned crank = cluster.block_rank(), csize = cluster.num_blocks();
     PhaseClock clk;
-    unsigned long long arcs = 0, atomics = 0, slots = 0;
+    unsigned long long arcs = 0, atomics = 0, slots = 0, pulled = 0;
 
     // phase 1: large graphs, one cluster per graph
     const int nlarge = (int)ld_relaxed(&bp.ctl->live.w[B_NLARGE]);
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(Threads, 512 / Threads * 2)
             const int t = *ticket0;
             cluster.sync();
             if (t < 0) break;
-            solve_graph<Algo>(bp, bp.order[t], dom, s_tmp, st, clk, arcs, atomics, slots);
+            solve_graph<Algo>(bp, bp.order[t], dom, s_tmp, st, clk, arcs, atomics, slots, pulled);
         }
     }
     // phase 2: the other graphs, one CTA per graph
@@ -167,13 +169,14 @@ __global__ void __launch_bounds__(Threads, 512 / Threads * 2)
             const int t = s_ticket;
             __syncthreads();
             if (t >= bp.G || status_of(bp.ctl) != 0) break;
-            solve_graph<Algo>(bp, bp.order[t], dom, s_tmp, st, clk, arcs, atomics, slots);
+            solve_graph<Algo>(bp, bp.order[t], dom, s_tmp, st, clk, arcs, atomics, slots, pulled);
             __syncthreads();
         }
     }
     block_sum_to(arcs, &bp.ctl->stats[kStArcs], s_red);
     block_sum_to(atomics, &bp.ctl->stats[kStAtomics], s_red);
     block_sum_to(slots, &bp.ctl->stats[kStSlots], s_red);
+    block_sum_to(pulled, &bp.ctl->stats[kStPulled], s_red);
     if (threadIdx.x == 0) {
         atomicMax(&bp.ctl->stats[kStKmax], st[kStKmax]);
         st[kStKmax] = 0;
@@ -194,9 +197,11 @@ size_t batched_ws_bytes(int G, long long total_n, long long total_m, int algo)
         for (int i = 0; i < 3; ++i) c.take<int>(total_n);
     } else {
         c.take<int2>(total_n);  // vinfo
-        c.take<int>(total_n);   // oldcore
+        c.take<int2>(total_n);  // mv[0]
+        c.take<int2>(total_n);  // mv[1]
         c.take<int>(total_m);   // histo
         for (int i = 0; i < 7; ++i) c.take<int>(total_n);
+        c.take<int2>(nchunks);  // chunk lists of every large vertex
     }
     c.take<int2>(nchunks);
     return c.size();
@@ -222,10 +227,12 @@ int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const 
         bp.qs = c.take<int>(total_n);
     } else {
         bp.vinfo = c.take<int2>(total_n);
-        bp.oldcore = c.take<int>(total_n);
+        bp.mv[0] = c.take<int2>(total_n);
+        bp.mv[1] = c.take<int2>(total_n);
         bp.histo = c.take<int>(total_m);
         for (int i = 0; i < 6; ++i) bp.lists[i] = c.take<int>(total_n);
         bp.us = c.take<int>(total_n);
+        bp.ichunks = c.take<int2>((size_t)(total_m / 16 + 2ll * G + 2));
     }
     bp.chunks = c.take<int2>((size_t)(total_m / 16 + 2ll * G + 2));
     bp.tn = cfg.tn;

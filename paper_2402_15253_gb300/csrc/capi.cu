@@ -9,6 +9,10 @@
 #include "pico_device.cuh"
 #include "pico_launch.h"
 
+static_assert(PICO_UPDATE_AUTO == pico::kUpdateAuto && PICO_UPDATE_PUSH == pico::kUpdatePush &&
+                  PICO_UPDATE_PULL == pico::kUpdatePull,
+              "update directions of the ABI and the kernels differ");
+
 namespace {
 
 struct DeviceState {
@@ -261,6 +265,8 @@ int pico_get_stats(pico_stream_t stream, pico_stats *out)
     out->slots = (int64_t)h.stats[pico::kStSlots];
     out->blocks = (int64_t)h.stats[pico::kStBlocks];
     out->scanned = (int64_t)h.stats[pico::kStScanned];
+    out->pulled = (int64_t)h.stats[pico::kStPulled];
+    out->pull_rounds = (int64_t)h.stats[pico::kStPullRounds];
     for (int i = 0; i < 8; ++i) {
         out->phase_ns[i] = (int64_t)h.stats[pico::kStPhaseNs + i];
         out->phase_count[i] = (int64_t)h.stats[pico::kStPhaseCount + i];
@@ -325,7 +331,9 @@ int pico_set_tuning(int small_deg, int chunk, int batched_threads, int cluster_l
     int rc = device_state(&d);
     if (rc != PICO_OK) return rc;
     std::lock_guard<std::mutex> lock(g_mu);
-    d->cfg.tn = pico::Tuning{small_deg, chunk, cluster_log2};
+    d->cfg.tn.small_deg = small_deg;
+    d->cfg.tn.chunk = chunk;
+    d->cfg.tn.cluster_log2 = cluster_log2;
     d->cfg.batched_threads = batched_threads;
     return PICO_OK;
 }
@@ -341,6 +349,31 @@ int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads, int *clust
     *chunk = d->cfg.tn.chunk;
     *batched_threads = d->cfg.batched_threads;
     *cluster_log2 = d->cfg.tn.cluster_log2;
+    return PICO_OK;
+}
+
+int pico_set_histo_update(int mode, int pull_pct)
+{
+    if (mode < PICO_UPDATE_AUTO || mode > PICO_UPDATE_PULL || pull_pct < 1 || pull_pct > 100)
+        return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_mu);
+    d->cfg.tn.update_mode = mode;
+    d->cfg.tn.pull_pct = pull_pct;
+    return PICO_OK;
+}
+
+int pico_get_histo_update(int *mode, int *pull_pct)
+{
+    if (!mode || !pull_pct) return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_mu);
+    *mode = d->cfg.tn.update_mode;
+    *pull_pct = d->cfg.tn.pull_pct;
     return PICO_OK;
 }
 

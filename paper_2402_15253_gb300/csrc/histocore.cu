@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ unsigned long long st[kStCount];   // statistics, written by thread 0
     if (threadIdx.x < kStCount) st[threadIdx.x] = 0;
     __syncthreads();
-    unsigned long long arcs = 0, atomics = 0, slots = 0;
+    unsigned long long arcs = 0, atomics = 0, slots = 0, pulled = 0;
     PhaseClock clk;
     if (blockIdx.x == 0 && threadIdx.x == 0 && last->trace_on) {
         last->trace_len = 0;
@@ -25,8 +25,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     clk.start();
     GridDom dom{p.ctl, s_snap, limit_ns};
-    histo::run(p, dom, s_tmp, st, clk, arcs, atomics, slots);
+    histo::run(p, dom, s_tmp, st, clk, arcs, atomics, slots, pulled);
     block_sum_to(arcs, &p.ctl->stats[kStArcs], s_red);
+    block_sum_to(pulled, &p.ctl->stats[kStPulled], s_red);
     block_sum_to(atomics, &p.ctl->stats[kStAtomics], s_red);
     block_sum_to(slots, &p.ctl->stats[kStSlots], s_red);
     if (blockIdx.x != 0 && threadIdx.x < kStCount) st[threadIdx.x] = 0;
@@ -40,11 +41,13 @@ size_t histocore_ws_bytes(long long n, long long m)
     Carver c(nullptr);
     c.take<Ctrl>(1);
     c.take<longlong2>(n);  // vinfo (sized for int64 offsets)
-    c.take<int>(n);        // oldcore
+    c.take<int2>(n);       // mv[0]
+    c.take<int2>(n);       // mv[1]
     c.take<int>(m);        // histo
     for (int i = 0; i < 6; ++i) c.take<int>(n);
     c.take<int>(n);        // us
-    c.take<int2>(chunk_capacity(m));
+    c.take<int2>(chunk_capacity(m));   // ub
+    c.take<int2>(chunk_capacity(m));   // ib
     return c.size();
 }
 
@@ -61,7 +64,8 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
     p.core = core;
     p.ctl = c.take<Ctrl>(1);
     p.vinfo = reinterpret_cast<histo::VRec<Off> *>(c.take<longlong2>(n));
-    p.oldcore = c.take<int>(n);
+    p.mv[0] = c.take<int2>(n);
+    p.mv[1] = c.take<int2>(n);
     p.histo = c.take<int>(m);
     for (int i = 0; i < 2; ++i) {
         p.tl[i] = c.take<int>(n);
@@ -71,6 +75,7 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
     p.us = c.take<int>(n);
     p.ub_cap = (unsigned)chunk_capacity(m);
     p.ub = c.take<int2>(p.ub_cap);
+    p.ib = c.take<int2>(p.ub_cap);
     p.zero_histo = false;
     p.tn = cfg.tn;
     if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;

@@ -12,9 +12,9 @@
 //               V_cnt = {v : deg v >= 1, histo[v][deg v] < deg v}.
 //   SumHisto    for v in V_cnt: sum the slots from core_old downwards until
 //               the running sum reaches the slot index k; core[v] <- k,
-//               oldcore[v] <- core_old, histo[v][k] <- sum (the new cnt).
+//               mv[v] <- {core_old, k}, histo[v][k] <- sum (the new cnt).
 //               By Thm. 2 every vertex of V_cnt changes.
-//   UpdateHisto for changed v (x = oldcore[v], y = core[v]) and neighbour u
+//   UpdateHisto for changed v (x = core_old, y = core[v]) and neighbour u
 //               with K = core[u] > y (types N1/N3 of Sec. IV-B): remove v
 //               from slot min(x, K), add it to slot y; u joins the next V_cnt
 //               when x >= K and slot K held exactly K before the decrement
@@ -24,6 +24,26 @@
 // new estimates) and UpdateHisto from the next SumHisto (all edits of a
 // round are in place before any vertex sums), which is the synchronous model
 // of Alg. 6.
+//
+// UpdateHisto direction. Alg. 6 pushes: each changed vertex v edits the rows
+// of its neighbours. On a large graph the rows edited in one round are spread
+// over far more memory than L2 holds, and almost every edit then misses. The
+// pull form issues the same edits from the other end: every vertex u whose
+// estimate is above the smallest new estimate of the round walks its own
+// adjacency and, for each neighbour w that changed in this round, applies
+// w's edit to u's row. With a symmetric adjacency both forms apply the same
+// multiset of edits (arc (v, u) pushed is arc (u, v) pulled), so the
+// histograms, the next V_cnt (decided by the same returning decrement of
+// slot K) and the result are identical; only the order of the edits differs,
+// and a warp pulling 32 consecutive rows edits one contiguous stretch of the
+// histogram. Pulling scans the arcs of every row that an edit can reach
+// instead of those of the changed vertices, so the auto mode pulls only in
+// rounds whose changed vertices hold at least pull_pct % of the arcs of a
+// graph with at least kPullMinArcs arcs. A vertex's {old, new} estimates are
+// kept per round parity (mv[r & 1]) so that pulling rows can tell whether a
+// neighbour changed in this round; SumHisto of round r clears the entries of
+// round r-1's changed vertices in the other buffer (their lists are intact
+// until UpdateHisto of round r appends to them).
 //
 // Load balance. V_cnt is kept as three lists by the estimate K that SumHisto
 // will walk down from: K <= 32 one thread per vertex, K <= 2048 one warp per
@@ -40,8 +60,13 @@ namespace histo {
 constexpr int kWarpK = 32;      // K above which a warp walks the histogram
 constexpr int kBlockK = 2048;   // K above which a CTA walks the histogram
 
-// live counters: V_cnt lists (T/W/B) per round parity, update lists, init chunks
-enum : int { L_T = 0, L_W = 1, L_B = 2, /* parity 1: 3..5 */ L_US = 6, L_UB = 7, L_IB = 8 };
+// live counters: V_cnt lists (T/W/B) per round parity, update lists, init
+// chunks, INT_MAX - smallest new estimate of the round, and the arcs of the
+// round's changed vertices (64-bit, two words, 8-byte aligned)
+enum : int {
+    L_T = 0, L_W = 1, L_B = 2, /* parity 1: 3..5 */ L_US = 6, L_UB = 7, L_IB = 8, L_YMIN = 9,
+    L_VOL = 10 /* and 11 */
+};
 
 // Per-vertex record {estimate, histogram base (= row_ptr[v])}: UpdateHisto
 // needs both for every neighbour it edits, and one 8-byte (16-byte with int64
@@ -67,12 +92,15 @@ struct Params {
     long long n, m;
     int *core;                    // output: coreness, written at the end
     VRec<Off> *vinfo;             // n records {estimate, histogram base}
-    int *oldcore;
+    int2 *mv[2];                  // per round parity: {old, new} estimate of the vertices
+                                  // changed in that round, {0, 0} for the others
     int *histo;                   // m slots (zeroed by run() when zero_histo)
     int *tl[2], *wl[2], *bl[2];   // V_cnt lists by class, per parity (n slots each)
     int *us;                      // changed vertices of small degree
     int2 *ub;                     // chunks of changed vertices of large degree
-    unsigned ub_cap;
+    int2 *ib;                     // chunks of every vertex of large degree (InitHisto and
+                                  // pull rounds; nullptr: InitHisto uses ub, never pull)
+    unsigned ub_cap;              // entries of ub, and of ib
     Ctrl *ctl;                    // status word (errors)
     bool zero_histo;
     Tuning tn;
@@ -86,7 +114,11 @@ struct InitArc {
     const VRec<Off> *vinfo;
     int *histo;
     unsigned long long n_arcs = 0;
-    __device__ __forceinline__ void item(int v, int &a, int &) { a = (int)__ldcg(vinfo + v).x; }
+    __device__ __forceinline__ bool item(int v, int &a, int &)
+    {
+        a = (int)__ldcg(vinfo + v).x;
+        return true;
+    }
     __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&)[kArcs],
                                          const int (&u)[kArcs], const Off (&rs)[kArcs],
                                          const int (&dv)[kArcs], const int (&)[kArcs])
@@ -103,11 +135,51 @@ struct InitArc {
     }
 };
 
+// Appends the vertices whose cnt fell below their estimate to the next
+// V_cnt, by the class of the estimate K (one aggregated append per class).
+template <int U>
+__device__ __forceinline__ void append_vcnt(const bool (&push)[U], const int (&vtx)[U],
+                                            const int (&K)[U], unsigned *live, int *tl, int *wl,
+                                            int *bl, unsigned cap, Ctrl *ctl)
+{
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+        const int cls = kclass(K[j]);
+        const unsigned p0 = warp_push(&live[L_T], push[j] && cls == 0);
+        const unsigned p1 = warp_push(&live[L_W], push[j] && cls == 1);
+        const unsigned p2 = warp_push(&live[L_B], push[j] && cls == 2);
+        if (push[j]) {
+            const unsigned pos = cls == 0 ? p0 : (cls == 1 ? p1 : p2);
+            if (pos >= cap) set_error(ctl, kErrNotConverged);
+            else if (cls == 0) tl[pos] = vtx[j];
+            else if (cls == 1) wl[pos] = vtx[j];
+            else bl[pos] = vtx[j];
+        }
+    }
+}
+
+// The edits of one arc between a changed vertex (estimate x -> y) and a vertex
+// u with estimate K and histogram row ru (types N1 and N3 of Sec. IV-B: only
+// when K > y). Returns true when u's cnt fell below K by this edit.
+template <typename Off>
+__device__ __forceinline__ bool edit_row(int *histo, Off ru, int K, int x, int y,
+                                         unsigned long long &n_atomics)
+{
+    if (K <= y) return false;
+    n_atomics += 2;
+    red_add(histo + ru + y - 1, 1);
+    if (x >= K)   // slot K holds cnt: its old value decides the append
+        return atomicSub(histo + ru + K - 1, 1) == K;
+    red_add(histo + ru + x - 1, -1);   // slot x < K: no append can follow
+    return false;
+}
+
+// Push form of UpdateHisto: arcs of the changed vertices.
 template <typename Off>
 struct UpdateArc {
     static constexpr int kArcs = 4;
     const VRec<Off> *vinfo;
-    const int *oldcore;
+    const int2 *mv;        // {old, new} estimates of this round
     int *histo;
     int *tl, *wl, *bl;
     Ctrl *ctl;
@@ -116,16 +188,18 @@ struct UpdateArc {
     unsigned cap;          // slots of each list (n)
     unsigned long long n_arcs = 0, n_atomics = 0;
 
-    __device__ __forceinline__ void item(int v, int &x, int &y)
+    __device__ __forceinline__ bool item(int v, int &x, int &y)
     {
-        x = ldcg(oldcore + v);
-        y = (int)__ldcg(vinfo + v).x;
+        const int2 r = __ldcg(mv + v);
+        x = r.x;
+        y = r.y;
+        return true;
     }
     __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&)[kArcs],
                                          const int (&u)[kArcs], const Off (&)[kArcs],
                                          const int (&x)[kArcs], const int (&y)[kArcs])
     {
-        int K[kArcs], old[kArcs];
+        int K[kArcs];
         Off ru[kArcs];
 #pragma unroll
         for (int j = 0; j < kArcs; ++j) {
@@ -134,55 +208,85 @@ struct UpdateArc {
             K[j] = (int)r.x;
             ru[j] = (Off)r.y;
         }
+        bool push[kArcs];
 #pragma unroll
         for (int j = 0; j < kArcs; ++j) {
-            old[j] = 0;
+            push[j] = false;
             if (valid[j]) {
                 ++n_arcs;
-                if (K[j] > y[j]) {   // types N1 and N3: the change is visible to u
-                    if (x[j] >= K[j]) {   // slot K holds cnt: its old value decides the append
-                        old[j] = atomicSub(histo + ru[j] + K[j] - 1, 1);
-                    } else {              // slot x < K: no append can follow
-                        red_add(histo + ru[j] + x[j] - 1, -1);
-                    }
-                    red_add(histo + ru[j] + y[j] - 1, 1);
-                    n_atomics += 2;
-                }
+                push[j] = edit_row(histo, ru[j], K[j], x[j], y[j], n_atomics);
             }
         }
-        unsigned *live = live_base + 3 * par;
-#pragma unroll
-        for (int j = 0; j < kArcs; ++j) {
-            const bool push = valid[j] && K[j] > y[j] && x[j] >= K[j] && old[j] == K[j];
-            const int cls = kclass(K[j]);
-            const unsigned p0 = warp_push(&live[L_T], push && cls == 0);
-            const unsigned p1 = warp_push(&live[L_W], push && cls == 1);
-            const unsigned p2 = warp_push(&live[L_B], push && cls == 2);
-            if (push) {
-                const unsigned pos = cls == 0 ? p0 : (cls == 1 ? p1 : p2);
-                if (pos >= cap) set_error(ctl, kErrNotConverged);
-                else if (cls == 0) tl[pos] = u[j];
-                else if (cls == 1) wl[pos] = u[j];
-                else bl[pos] = u[j];
-            }
-        }
+        append_vcnt(push, u, K, live_base + 3 * par, tl, wl, bl, cap, ctl);
     }
 };
 
-// Records the result of SumHisto for v. Returns the degree of v, or -1 when
-// v did not change (impossible on a valid graph by Thm. 2).
+// Pull form of UpdateHisto: arcs of every vertex u whose estimate K is above
+// the smallest new estimate of the round; the edit of arc (u, w) is the one
+// w's push would make to u's row, when w changed in this round.
 template <typename Off>
-__device__ __forceinline__ long long sum_apply(const Params<Off> &p, int v, Off rs, int K,
-                                               int h, int sum)
+struct PullArc {
+    static constexpr int kArcs = 4;
+    const VRec<Off> *vinfo;
+    const int2 *mv;        // {old, new} estimates of this round ({0, 0}: unchanged)
+    int *histo;
+    int *tl, *wl, *bl;
+    Ctrl *ctl;
+    unsigned *live_base;
+    int par;
+    unsigned cap;
+    int ymin;              // no row with K <= ymin can be edited
+    unsigned long long n_arcs = 0, n_atomics = 0;
+
+    __device__ __forceinline__ bool item(int u, int &K, int &)
+    {
+        K = (int)__ldcg(vinfo + u).x;
+        return K > ymin;
+    }
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&uu)[kArcs],
+                                         const int (&w)[kArcs], const Off (&ru)[kArcs],
+                                         const int (&K)[kArcs], const int (&)[kArcs])
+    {
+        int2 r[kArcs];
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) r[j] = valid[j] ? __ldcg(mv + w[j]) : make_int2(0, 0);
+        bool push[kArcs];
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            push[j] = false;
+            if (valid[j]) {
+                ++n_arcs;
+                if (r[j].x != 0) push[j] = edit_row(histo, ru[j], K[j], r[j].x, r[j].y, n_atomics);
+            }
+        }
+        append_vcnt(push, uu, K, live_base + 3 * par, tl, wl, bl, cap, ctl);
+    }
+};
+
+// Per-thread totals of the vertices a thread changed in SumHisto.
+struct RoundAcc {
+    unsigned long long arcs = 0;   // their degrees
+    int ymin = INT_MAX;            // their smallest new estimate
+};
+
+// Records the result of SumHisto for v (estimate K -> h) in round parity
+// par. Returns the degree of v, or -1 when v did not change (impossible on a
+// valid graph by Thm. 2).
+template <typename Off>
+__device__ __forceinline__ long long sum_apply(const Params<Off> &p, int par, int v, Off rs, int K,
+                                               int h, int sum, RoundAcc &acc)
 {
     if (h >= K || h < 1) {
         set_error(p.ctl, kErrBadGraph);
         return -1;
     }
     p.vinfo[v].x = h;
-    p.oldcore[v] = K;
+    p.mv[par][v] = make_int2(K, h);
     p.histo[rs + h - 1] = sum;
-    return (long long)(p.rp[v + 1] - rs);
+    const long long d = (long long)(p.rp[v + 1] - rs);
+    acc.arcs += (unsigned long long)d;
+    acc.ymin = h < acc.ymin ? h : acc.ymin;
+    return d;
 }
 
 // Lists a changed vertex of degree d for UpdateHisto (single-thread path).
@@ -201,16 +305,16 @@ __device__ __forceinline__ void list_changed(const Params<Off> &p, unsigned *liv
 }
 
 template <typename Off>
-__device__ __forceinline__ void sum_done(const Params<Off> &p, unsigned *live, int v, Off rs,
-                                         int K, int h, int sum)
+__device__ __forceinline__ void sum_done(const Params<Off> &p, int par, unsigned *live, int v,
+                                         Off rs, int K, int h, int sum, RoundAcc &acc)
 {
-    list_changed(p, live, v, sum_apply(p, v, rs, K, h, sum));
+    list_changed(p, live, v, sum_apply(p, par, v, rs, K, h, sum, acc));
 }
 
 // SumHisto by one CTA for a vertex with a large estimate.
 template <typename Off>
-__device__ void sum_block(const Params<Off> &p, unsigned *live, int v, int *s,
-                          unsigned long long &slots)
+__device__ void sum_block(const Params<Off> &p, int par, unsigned *live, int v, int *s,
+                          unsigned long long &slots, RoundAcc &acc)
 {
     const VRec<Off> rec = __ldcg(p.vinfo + v);
     const Off rs = (Off)rec.y;
@@ -247,7 +351,7 @@ __device__ void sum_block(const Params<Off> &p, unsigned *live, int v, int *s,
         if (first != INT_MAX) {
             if ((int)threadIdx.x == first) {
                 slots += (unsigned long long)(K - slot + 1);
-                sum_done(p, live, v, rs, K, slot, run);
+                sum_done(p, par, live, v, rs, K, slot, run, acc);
             }
             __syncthreads();
             return;
@@ -260,8 +364,8 @@ __device__ void sum_block(const Params<Off> &p, unsigned *live, int v, int *s,
 
 // SumHisto by one warp for a vertex with a medium estimate.
 template <typename Off>
-__device__ __forceinline__ void sum_warp(const Params<Off> &p, unsigned *live, int v,
-                                         unsigned long long &slots)
+__device__ __forceinline__ void sum_warp(const Params<Off> &p, int par, unsigned *live, int v,
+                                         unsigned long long &slots, RoundAcc &acc)
 {
     const int lane = threadIdx.x & 31;
     const VRec<Off> rec = __ldcg(p.vinfo + v);
@@ -283,7 +387,7 @@ __device__ __forceinline__ void sum_warp(const Params<Off> &p, unsigned *live, i
             const int L = __ffs(b) - 1;
             if (lane == L) {
                 slots += (unsigned long long)(K - slot + 1);
-                sum_done(p, live, v, rs, K, slot, run);
+                sum_done(p, par, live, v, rs, K, slot, run, acc);
             }
             return;
         }
@@ -295,8 +399,8 @@ __device__ __forceinline__ void sum_warp(const Params<Off> &p, unsigned *live, i
 // SumHisto by one thread for a vertex with a small estimate; returns the
 // vertex degree (or -1, see sum_apply).
 template <typename Off>
-__device__ __forceinline__ long long sum_thread(const Params<Off> &p, int v,
-                                                unsigned long long &slots)
+__device__ __forceinline__ long long sum_thread(const Params<Off> &p, int par, int v,
+                                                unsigned long long &slots, RoundAcc &acc)
 {
     const VRec<Off> rec = __ldcg(p.vinfo + v);
     const Off rs = (Off)rec.y;
@@ -307,15 +411,42 @@ __device__ __forceinline__ long long sum_thread(const Params<Off> &p, int v,
         if (sum >= k) break;
     }
     slots += (unsigned long long)(K - k + 1);
-    return sum_apply(p, v, rs, K, k, sum);
+    return sum_apply(p, par, v, rs, K, k, sum, acc);
+}
+
+// Whether UpdateHisto of this round pulls (see the direction note above);
+// vol: arcs of the round's changed vertices. Uniform over the domain.
+template <typename Off>
+__device__ __forceinline__ bool pull_round(const Params<Off> &p, unsigned long long vol)
+{
+    if (p.ib == nullptr || p.tn.update_mode == kUpdatePush) return false;
+    if (p.tn.update_mode == kUpdatePull) return true;
+    return p.m >= kPullMinArcs &&
+           vol * 100ull >= (unsigned long long)p.tn.pull_pct * (unsigned long long)p.m;
+}
+
+// Adds the warp's round totals to the domain's counters (lane 0 of each warp).
+__device__ __forceinline__ void fold_round(const RoundAcc &acc, unsigned *live)
+{
+    unsigned long long a = acc.arcs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(kFull, a, o);
+    const int ym = __reduce_min_sync(kFull, acc.ymin);
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(reinterpret_cast<unsigned long long *>(&live[L_VOL]), a);
+        if (ym != INT_MAX) atomicMax(&live[L_YMIN], (unsigned)(INT_MAX - ym));
+    }
 }
 
 // HistoCore on one graph. Every thread of the domain calls it. st: per-CTA
 // statistics in shared memory (thread 0 writes); s_tmp: >= 256 shared words.
+// arcs counts InitHisto's arcs plus the arcs of every round's changed vertices
+// (the arcs Alg. 6 scans, whatever the direction); pulled counts the arcs
+// that pull rounds scanned.
 template <typename Off, typename Dom>
 __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned long long *st,
                     PhaseClock &clk, unsigned long long &arcs, unsigned long long &atomics,
-                    unsigned long long &slots)
+                    unsigned long long &slots, unsigned long long &pulled)
 {
     const Params<Off> &p = p0;
     Ctrl *ctl = p.ctl;
@@ -325,11 +456,12 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
     const unsigned gwarp = tid >> 5, nwarps = nthreads >> 5;
     const long long n = p.n;
     const long long first = (long long)dom.cta() * blockDim.x;
+    int2 *const ilist = p.ib ? p.ib : p.ub;   // chunks of every large vertex
 
     if (p.zero_histo) {
         for (long long i = first + threadIdx.x; i < p.m; i += nthreads) p.histo[i] = 0;
     }
-    // core = degree; chunk list of the large vertices for InitHisto
+    // core = degree; no vertex changed yet; chunk list of the large vertices
     for (long long base = first; base < n; base += nthreads) {
         const long long v = base + threadIdx.x;
         long long d = 0;
@@ -337,24 +469,26 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
             const Off r0 = p.rp[v];
             d = (long long)(p.rp[v + 1] - r0);
             p.vinfo[v] = make_vrec<Off>((int)d, r0);
+            p.mv[0][v] = make_int2(0, 0);
+            p.mv[1][v] = make_int2(0, 0);
         }
         const unsigned nch =
             d > p.tn.small_deg ? (unsigned)((d + p.tn.chunk - 1) / p.tn.chunk) : 0u;
         const unsigned pos = block_alloc(nch, &live[L_IB], s_tmp);
         if (nch && (unsigned long long)pos + nch <= p.ub_cap)
-            for (unsigned c = 0; c < nch; ++c) p.ub[pos + c] = make_int2((int)v, (int)c);
+            for (unsigned c = 0; c < nch; ++c) ilist[pos + c] = make_int2((int)v, (int)c);
         else if (nch)
             set_error(ctl, kErrNotConverged);
     }
     if (!dom.sync()) return;
     if (threadIdx.x == 0) ++st[kStBarriers];
     if (Dom::kGrid) clk.end(st, kPhInit);
+    const unsigned nib = snap[L_IB];
 
     // InitHisto
     {
         InitArc<Off> f{p.vinfo, p.histo};
-        expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, p.ub, snap[L_IB], gwarp, nwarps, f,
-               p.tn);
+        expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, ilist, nib, gwarp, nwarps, f, p.tn);
         arcs += f.n_arcs;
         atomics += f.n_arcs;
     }
@@ -383,8 +517,9 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
     if (Dom::kGrid) clk.end(st, kPhInit);
 
     const long long max_rounds = p.m + 2;
+    unsigned pt = 0, pw = 0, pb = 0;   // V_cnt sizes of the previous round
     for (long long r = 0;; ++r) {
-        const int par = (int)(r & 1);
+        const int par = (int)(r & 1), np = 1 - par;
         const unsigned nt = snap[3 * par + L_T], nwl = snap[3 * par + L_W],
                        nb = snap[3 * par + L_B];
         if (nt + nwl + nb == 0) break;
@@ -397,22 +532,33 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
             st[kStFrontier] += nt + nwl + nb;
         }
         if (dom.leader()) {
-            const int np = 1 - par;
             live[3 * np + L_T] = 0;
             live[3 * np + L_W] = 0;
             live[3 * np + L_B] = 0;
         }
+        // the previous round's changed vertices are not changed in this one:
+        // clear their entries of the other parity (read by nobody until the
+        // next round's UpdateHisto; their lists are intact until this round's)
+        for (long long i = first + threadIdx.x; i < (long long)pt + pw + pb; i += nthreads) {
+            const unsigned k = (unsigned)i;
+            const int v = k < pt ? ldcg(p.tl[np] + k)
+                                 : (k < pt + pw ? ldcg(p.wl[np] + (k - pt))
+                                                : ldcg(p.bl[np] + (k - pt - pw)));
+            p.mv[np][v] = make_int2(0, 0);
+        }
         // SumHisto: CTA items, then warp items, then thread items
+        RoundAcc acc;
         for (unsigned i = dom.cta(); i < nb; i += dom.ncta())
-            sum_block(p, live, ldcg(p.bl[par] + i), (int *)s_tmp, slots);
-        for (unsigned i = gwarp; i < nwl; i += nwarps) sum_warp(p, live, ldcg(p.wl[par] + i), slots);
+            sum_block(p, par, live, ldcg(p.bl[par] + i), (int *)s_tmp, slots, acc);
+        for (unsigned i = gwarp; i < nwl; i += nwarps)
+            sum_warp(p, par, live, ldcg(p.wl[par] + i), slots, acc);
         for (long long base = first; base < nt; base += nthreads) {
             const long long i = base + threadIdx.x;
             int v = 0;
             long long d = -1;
             if (i < nt) {
                 v = ldcg(p.tl[par] + i);
-                d = sum_thread(p, v, slots);
+                d = sum_thread(p, par, v, slots, acc);
             }
             const bool small = d >= 0 && d <= p.tn.small_deg;
             unsigned pos, unused;
@@ -423,19 +569,38 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
             }
             if (d > p.tn.small_deg) list_changed(p, live, v, d);
         }
+        fold_round(acc, live);
         if (!dom.sync()) return;
         if (threadIdx.x == 0) ++st[kStBarriers];
         if (Dom::kGrid) clk.end(st, kPhSumHisto, nt + nwl + nb);
+        pt = nt;
+        pw = nwl;
+        pb = nb;
 
-        // UpdateHisto over the changed vertices
+        // UpdateHisto over the changed vertices, pushed or pulled
         const unsigned nus = snap[L_US], nub = snap[L_UB];
+        const unsigned long long vol =
+            (unsigned long long)snap[L_VOL] | ((unsigned long long)snap[L_VOL + 1] << 32);
+        const int ymin = INT_MAX - (int)snap[L_YMIN];
         if (dom.leader()) {
             live[L_US] = 0;
             live[L_UB] = 0;
+            live[L_YMIN] = 0;
+            live[L_VOL] = 0;
+            live[L_VOL + 1] = 0;
         }
-        {
-            const int np = 1 - par;
-            UpdateArc<Off> f{p.vinfo, p.oldcore, p.histo, p.tl[np], p.wl[np], p.bl[np],
+        const bool pull = pull_round(p, vol);
+        if (pull) {
+            PullArc<Off> f{p.vinfo, p.mv[par], p.histo, p.tl[np], p.wl[np], p.bl[np],
+                           ctl,     live,      np,      (unsigned)n, ymin};
+            expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, ilist, nib, gwarp, nwarps, f,
+                   p.tn, batch_width((unsigned)n, nib, nwarps));
+            arcs += acc.arcs;
+            pulled += f.n_arcs;
+            atomics += f.n_atomics;
+            if (threadIdx.x == 0) ++st[kStPullRounds];
+        } else {
+            UpdateArc<Off> f{p.vinfo, p.mv[par], p.histo, p.tl[np], p.wl[np], p.bl[np],
                              ctl,     live,      np,      (unsigned)n};
             expand(p.rp, p.ci, p.us, nus, p.ub, nub, gwarp, nwarps, f, p.tn,
                    batch_width(nus, nub, nwarps));
@@ -444,7 +609,7 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         }
         if (!dom.sync()) return;
         if (threadIdx.x == 0) ++st[kStBarriers];
-        if (Dom::kGrid) clk.end(st, kPhUpdateHisto, nus + nub);
+        if (Dom::kGrid) clk.end(st, pull ? kPhUpdatePull : kPhUpdateHisto, pull ? (unsigned)n : nus + nub);
     }
     // the estimates are the coreness now (no vertex has cnt < estimate)
     for (long long v = first + threadIdx.x; v < n; v += nthreads) p.core[v] = (int)__ldcg(p.vinfo + v).x;

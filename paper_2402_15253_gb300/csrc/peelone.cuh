@@ -65,7 +65,7 @@ struct Arc {
     Tuning tn;
     unsigned long long n_arcs = 0, n_atomics = 0;
 
-    __device__ __forceinline__ void item(int, int &, int &) {}
+    __device__ __forceinline__ bool item(int, int &, int &) { return true; }
 
     __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&)[kArcs],
                                          const int (&u)[kArcs], const Off (&)[kArcs],

@@ -32,10 +32,20 @@ constexpr int kChunk = 256;       // default chunk size
 constexpr int kMinSmallDeg = 32, kMaxSmallDeg = 256;
 constexpr int kMinChunk = 64, kMaxChunk = 4096;
 
+// Direction of HistoCore's UpdateHisto: push from the changed vertices (the
+// formulation of Alg. 6), pull into every vertex whose row an edit can reach,
+// or choose per round (auto).
+constexpr int kUpdateAuto = 0, kUpdatePush = 1, kUpdatePull = 2;
+constexpr int kPullPct = 40;                  // auto: pull when the changed vertices
+                                              // hold >= this % of the arcs ...
+constexpr long long kPullMinArcs = 1ll << 22;  // ... of a graph with at least this many
+
 struct Tuning {
     int small_deg;
     int chunk;
     int cluster_log2;   // batched form: graphs with >= 2^cluster_log2 arcs use a cluster
+    int update_mode = kUpdateAuto;
+    int pull_pct = kPullPct;
 };
 constexpr int kClusterNever = 62;   // cluster_log2 value that disables clusters
 constexpr int kClusterLog2 = 21;    // default
@@ -56,7 +66,8 @@ struct alignas(128) Line {
 // Statistics slots (match pico_stats field order after `algo`).
 enum StatIdx : int {
     kStLevels = 0, kStKmax, kStSubrounds, kStScans, kStRounds, kStFrontier,
-    kStBarriers, kStArcs, kStAtomics, kStSlots, kStBlocks, kStScanned,
+    kStBarriers, kStArcs, kStAtomics, kStSlots, kStBlocks, kStScanned, kStPulled,
+    kStPullRounds,
     kStPhaseNs = 16,      // 16..23: device time per phase kind (CTA 0's view)
     kStPhaseCount = 24,   // 24..31: phases per kind
     kStCount = 32
@@ -65,7 +76,8 @@ enum StatIdx : int {
 // Phase kinds for the timing statistics.
 enum PhaseKind : int {
     kPhInit = 0, kPhScan, kPhWaveTiny, kPhWaveMid, kPhWaveWide, kPhInitHisto, kPhSumHisto,
-    kPhUpdateHisto
+    kPhUpdateHisto,
+    kPhUpdatePull   // trace only: counted as kPhUpdateHisto in the statistics
 };
 
 
@@ -121,8 +133,9 @@ struct PhaseClock {
     {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const unsigned long long t = gtime();
-            st[kStPhaseNs + kind] += t - t_prev;
-            st[kStPhaseCount + kind] += 1;
+            const int sk = kind > kPhUpdateHisto ? kPhUpdateHisto : kind;
+            st[kStPhaseNs + sk] += t - t_prev;
+            st[kStPhaseCount + sk] += 1;
             if (trace && *trace_len < (unsigned)kTraceCap) {
                 trace[*trace_len] = TraceEntry{(unsigned)kind, units, t - t_prev};
                 ++*trace_len;
@@ -380,7 +393,8 @@ __device__ __forceinline__ void red_add(int *p, int v)
 }
 
 // Functor interface used by expand() (U = F::kArcs):
-//   void item(int v, int &a, int &b)     per-vertex prologue (lane-local)
+//   bool item(int v, int &a, int &b)     per-vertex prologue (lane-local);
+//                                        false skips the vertex's arcs
 //   void arcs(const bool (&valid)[U], const int (&v)[U], const int (&u)[U],
 //             const Off (&rs)[U], const int (&a)[U], const int (&b)[U])
 //                                        called by ALL 32 lanes together with
@@ -422,7 +436,7 @@ __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__
                 const Off dd = rp[v + 1] - rs;
                 if (dd <= tn.small_deg) {
                     d = (int)dd;
-                    if (d > 0) f.item(v, a, b);
+                    if (d > 0 && !f.item(v, a, b)) d = 0;
                 }
             }
             int incl = d;
@@ -463,7 +477,7 @@ __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__
             const Off s = rs + (Off)ent.y * tn.chunk;
             const Off t = (s + tn.chunk < re) ? s + tn.chunk : re;
             int a = 0, b = 0;
-            f.item(v, a, b);
+            if (!f.item(v, a, b)) continue;
             for (Off e0 = s; e0 < t; e0 += 32 * U) {
                 bool valid[U];
                 int vo[U], u[U], ao[U], bo[U];

@@ -74,6 +74,10 @@ def test_argument_checks_need_no_gpu(lib):
     # an empty graph is a no-op
     assert L.pico_coreness(vp(None), vp(None), ctypes.c_int64(0), ctypes.c_int64(0), vp(None),
                            0, vp(None)) == pico.PICO_OK
+    # UpdateHisto direction: unknown modes and thresholds outside 1..100
+    for mode, pct in ((-1, 25), (3, 25), (pico.PICO_UPDATE_AUTO, 0), (pico.PICO_UPDATE_PULL, 101)):
+        assert L.pico_set_histo_update(mode, pct) == pico.PICO_ERR_INVALID_ARG
+    assert L.pico_get_histo_update(vp(None), vp(None)) == pico.PICO_ERR_INVALID_ARG
 
 
 def test_binding_names_mirror_the_abi(lib):

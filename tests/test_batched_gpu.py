@@ -129,3 +129,21 @@ def test_large_graphs_solved_by_clusters(pico, algo):
     pb = gg.pack_graphs(graphs)
     got = run_batch(pico, pb, algo)
     assert np.array_equal(got, oracle_batch(pb))
+
+
+def test_batch_with_pulled_updates(pico):
+    """HistoCore with every UpdateHisto pulled, on a batch of small graphs
+    (one CTA each) and large ones (one cluster each): same results."""
+    graphs = [gg.rmat_graph(17, 16, 64), gg.grid_graph(300, 200)]
+    graphs += [gg.spec_graph(s) for s in gg.batch_specs(40, 65, nmin=30, nmax=20000)]
+    graphs.insert(7, gg.from_edge_list([], 0))
+    pb = gg.pack_graphs(graphs)
+    want = oracle_batch(pb)
+    assert pico.pico_set_histo_update(pico.PICO_UPDATE_PULL, 25) == 0
+    try:
+        got = run_batch(pico, pb, "histocore")
+        st = pico.pico_get_stats()
+    finally:
+        pico.pico_set_histo_update(pico.PICO_UPDATE_AUTO, pico.PULL_PCT_DEFAULT)
+    assert np.array_equal(got, want)
+    assert st["pull_rounds"] > 0 and st["pulled"] > 0

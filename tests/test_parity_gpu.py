@@ -157,6 +157,56 @@ def test_families_match_oracle(pico, algo, name, make):
         assert st["rounds"] == ost["rounds"]
         assert st["frontier"] == ost["frontier"]
         assert st["slots"] == ost["slots_read"]
+        # InitHisto's arcs and edits, then the rounds' (either direction)
+        assert st["arcs"] == g.arcs + ost["arcs_scanned"]
+        assert st["atomics"] == g.arcs + 2 * ost["updates"]
+
+
+@pytest.fixture
+def update_mode(pico):
+    """Sets the UpdateHisto direction for one test, then restores auto."""
+    def set_mode(name):
+        assert pico.pico_set_histo_update(pico.UPDATES[name], 25) == 0
+        assert pico.pico_get_histo_update() == (pico.UPDATES[name], 25)
+    yield set_mode
+    assert pico.pico_set_histo_update(pico.PICO_UPDATE_AUTO, pico.PULL_PCT_DEFAULT) == 0
+
+
+@pytest.mark.parametrize("mode", ["push", "pull"])
+@pytest.mark.parametrize("name,make", FAMILIES, ids=[f[0] for f in FAMILIES])
+def test_histocore_update_directions(pico, update_mode, mode, name, make):
+    """Pushed and pulled UpdateHisto apply the same edits: the result, the
+    rounds, the frontier and the edit count all equal the oracle's Alg. 6."""
+    g = make()
+    rp, ci = g.numpy()
+    update_mode(mode)
+    got, st = run(pico, g, "histocore")
+    assert_same(got, oracle.bz_coreness(rp, ci), f"{name} {mode}")
+    _, ost = oracle.histocore(rp, ci)
+    assert st["rounds"] == ost["rounds"]
+    assert st["frontier"] == ost["frontier"]
+    assert st["slots"] == ost["slots_read"]
+    assert st["arcs"] == g.arcs + ost["arcs_scanned"]
+    assert st["atomics"] == g.arcs + 2 * ost["updates"]
+    if mode == "pull":
+        assert st["pull_rounds"] == st["rounds"] and st["pulled"] > 0
+    else:
+        assert st["pull_rounds"] == 0 and st["pulled"] == 0
+
+
+def test_histocore_auto_pulls_large_rounds(pico, update_mode):
+    """R-MAT scale 18 (8.4 M arcs): the auto mode pulls the first rounds,
+    whose changed vertices hold most arcs, and pushes the later ones."""
+    g = gg.rmat_graph(18, 16, 36)
+    assert g.arcs >= 1 << 22
+    rp, ci = g.numpy()
+    update_mode("auto")
+    got, st = run(pico, g, "histocore")
+    assert_same(got, oracle.bz_coreness(rp, ci), "rmat18 auto")
+    assert 0 < st["pull_rounds"] < st["rounds"]
+    _, ost = oracle.histocore(rp, ci)
+    assert st["rounds"] == ost["rounds"]
+    assert st["atomics"] == g.arcs + 2 * ost["updates"]
 
 
 @pytest.mark.parametrize("algo", ALGOS)
