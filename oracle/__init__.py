@@ -70,6 +70,9 @@ def lib():
             L.oracle_peelone.argtypes = [i64, p64, p32, p32, p64]
             L.oracle_histocore.argtypes = [i64, p64, p32, p32, p64, ctypes.c_int]
             L.oracle_check.argtypes = [i64, p64, p32, p32, p64]
+            for f in (L.oracle_gpp, L.oracle_nbrcore, L.oracle_cntcore):
+                f.argtypes = [i64, p64, p32, p32, p64]
+                f.restype = ctypes.c_int
             for f in (L.oracle_bz, L.oracle_bz_batched, L.oracle_hindex_jacobi,
                       L.oracle_peelone, L.oracle_histocore, L.oracle_check):
                 f.restype = ctypes.c_int
@@ -152,6 +155,39 @@ def histocore(row_ptr, col_idx, check: bool = False):
         raise MemoryError
     keys = ("rounds", "frontier", "slots_read", "arcs_scanned", "updates", "violations")
     return out, dict(zip(keys, (int(x) for x in st)))
+
+
+def gpp(row_ptr, col_idx):
+    """Alg. 3 (General Parallel Peel) in synchronous steps; returns
+    (core, stats dict)."""
+    rp, ci, n = _csr(_np(row_ptr), _np(col_idx))
+    out = np.zeros(n, dtype=np.int32)
+    st = np.zeros(5, dtype=np.int64)
+    if lib().oracle_gpp(n, _p64(rp), _p32(ci), _p32(out), _p64(st)) != 0:
+        raise MemoryError
+    keys = ("steps", "scans", "decrements", "arcs_scanned", "kmax")
+    return out, dict(zip(keys, (int(x) for x in st)))
+
+
+def _index2core(fn, row_ptr, col_idx):
+    rp, ci, n = _csr(_np(row_ptr), _np(col_idx))
+    out = np.zeros(n, dtype=np.int32)
+    st = np.zeros(5, dtype=np.int64)
+    if fn(n, _p64(rp), _p32(ci), _p32(out), _p64(st)) != 0:
+        raise MemoryError
+    keys = ("rounds", "active", "frontier", "arcs_scanned", "violations")
+    return out, dict(zip(keys, (int(x) for x in st)))
+
+
+def nbrcore(row_ptr, col_idx):
+    """NbrCore (neighbours of changed vertices recompute HINDEX), synchronous;
+    returns (core, stats dict)."""
+    return _index2core(lib().oracle_nbrcore, row_ptr, col_idx)
+
+
+def cntcore(row_ptr, col_idx):
+    """CntCore (Alg. 5), synchronous; returns (core, stats dict)."""
+    return _index2core(lib().oracle_cntcore, row_ptr, col_idx)
 
 
 def check(row_ptr, col_idx, core) -> dict:

@@ -21,6 +21,10 @@
  *                        frontier processed in waves; counts levels and waves.
  *   oracle_histocore     Alg. 6 (HistoCore) run sequentially round by round,
  *                        with an optional check of the histogram invariant.
+ *   oracle_gpp           Alg. 3 (General Parallel Peel, the baseline of
+ *                        Sec. V) run in its synchronous scan/scatter steps.
+ *   oracle_nbrcore       NbrCore and CntCore (Alg. 5), the Index2core
+ *   oracle_cntcore       baselines of Sec. IV-A and V, run synchronously.
  *   oracle_check         fixpoint and certificate checks of a coreness vector.
  *
  * Graphs are CSR: row_ptr (int64, n + 1 entries), col_idx (int32, row_ptr[n]
@@ -357,6 +361,152 @@ int oracle_histocore(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *c
     free(histo); free(oldcore); free(cur); free(nxt); free(mark); free(cnt);
     if (stats) memcpy(stats, st, sizeof(st));
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 3, General Parallel Peel, run sequentially in its synchronous form.
+   deg[] (residual degree) and rem[] (removed flag) are separate arrays;
+   core[] receives the level at which a vertex is removed. Each step scans
+   every vertex for the frontier {v : !rem[v], deg[v] <= k}; an empty scan
+   raises k by one; otherwise the frontier gets core = k and rem = 1, and the
+   scatter lowers deg[u] of every non-removed neighbour u by one. Isolated
+   vertices leave at k = 0.
+   stats[0] = scatter steps (scans with a non-empty frontier),
+   stats[1] = scans (including the empty ones that raise k),
+   stats[2] = decrements, stats[3] = arcs scanned from frontiers,
+   stats[4] = largest k that removed a vertex.                              */
+/* ------------------------------------------------------------------------ */
+int oracle_gpp(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *core,
+               int64_t *stats)
+{
+    int64_t st[5] = {0, 0, 0, 0, 0};
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t *deg = (int32_t *)malloc(nn * sizeof(int32_t));
+    uint8_t *rem = (uint8_t *)calloc(nn, 1);
+    int32_t *front = (int32_t *)malloc(nn * sizeof(int32_t));
+    if (!deg || !rem || !front) { free(deg); free(rem); free(front); return -1; }
+    for (int64_t v = 0; v < n; ++v) deg[v] = DEG(rp, v);
+    int64_t nres = n;
+    int32_t k = 0;
+    while (nres > 0) {
+        st[1]++;
+        int64_t nf = 0;
+        for (int64_t v = 0; v < n; ++v)
+            if (!rem[v] && deg[v] <= k) front[nf++] = (int32_t)v;
+        if (nf == 0) { k++; continue; }
+        for (int64_t i = 0; i < nf; ++i) {
+            core[front[i]] = k;
+            rem[front[i]] = 1;
+        }
+        nres -= nf;
+        st[0]++;
+        st[4] = k;
+        for (int64_t i = 0; i < nf; ++i) {
+            int32_t v = front[i];
+            st[3] += DEG(rp, v);
+            for (int64_t e = rp[v]; e < rp[v + 1]; ++e)
+                if (!rem[ci[e]]) { deg[ci[e]]--; st[2]++; }
+        }
+    }
+    free(deg); free(rem); free(front);
+    if (stats) memcpy(stats, st, sizeof(st));
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The Index2core variants of Sec. IV-A and the evaluation, run
+   synchronously (every round reads the previous round's estimates).
+   Estimates start at the degree. The active set starts as every vertex of
+   degree >= 1.
+   nbrcore (NbrCore): every active vertex recomputes HINDEX of its
+     neighbours' estimates; the vertices whose estimate fell form C, and the
+     next active set is the union of their neighbourhoods.
+   cntcore (CntCore, Alg. 5): every active vertex counts cnt = the neighbours
+     whose estimate is >= its own; the frontier is {cnt < estimate}, whose
+     vertices recompute HINDEX (they all fall, by Thm. 2; a frontier vertex
+     that keeps its estimate counts as a violation). The next active set is
+     the union of the frontier's neighbourhoods.
+   Both stop after a round in which no estimate changes (for CntCore, by
+   Thm. 2, a round whose frontier is empty).
+   stats[0] = rounds that changed an estimate, stats[1] = sum of active-set
+   sizes over all rounds executed, stats[2] = sum of the changed (NbrCore)
+   or frontier (CntCore) sizes, stats[3] = arcs scanned (HINDEX and cnt each
+   read the whole adjacency), stats[4] = violations.                        */
+/* ------------------------------------------------------------------------ */
+static int index2core_sync(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *core,
+                           int64_t *stats, int use_cnt)
+{
+    int64_t st[5] = {0, 0, 0, 0, 0};
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t md = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        core[v] = DEG(rp, v);
+        if (core[v] > md) md = core[v];
+    }
+    int32_t *act = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *nxt = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *chg = (int32_t *)malloc(nn * sizeof(int32_t));
+    int32_t *newv = (int32_t *)malloc(nn * sizeof(int32_t));
+    uint8_t *mark = (uint8_t *)calloc(nn, 1);
+    int64_t *cnt = (int64_t *)malloc(((size_t)md + 2) * sizeof(int64_t));
+    if (!act || !nxt || !chg || !newv || !mark || !cnt) {
+        free(act); free(nxt); free(chg); free(newv); free(mark); free(cnt);
+        return -1;
+    }
+    int64_t nact = 0;
+    for (int64_t v = 0; v < n; ++v)
+        if (DEG(rp, v) > 0) act[nact++] = (int32_t)v;
+    while (nact > 0) {
+        st[1] += nact;
+        int64_t nchg = 0, nfront = 0;
+        for (int64_t i = 0; i < nact; ++i) {
+            int32_t v = act[i], d = DEG(rp, v);
+            if (use_cnt) {
+                int64_t c = 0;
+                for (int64_t e = rp[v]; e < rp[v + 1]; ++e) c += (core[ci[e]] >= core[v]);
+                st[3] += d;
+                if (c >= core[v]) continue;   /* not in the frontier */
+            }
+            int32_t h = hindex_of(rp, ci, core, v, core[v] < d ? core[v] : d, cnt);
+            st[3] += d;
+            if (use_cnt) nfront++;
+            if (h < core[v]) {
+                chg[nchg] = v;
+                newv[nchg++] = h;
+            } else if (use_cnt) {
+                st[4]++;   /* a frontier vertex that kept its estimate */
+            }
+        }
+        st[2] += use_cnt ? nfront : nchg;
+        if (nchg == 0) break;
+        st[0]++;
+        /* apply after every vertex of the round has read the old estimates */
+        for (int64_t i = 0; i < nchg; ++i) core[chg[i]] = newv[i];
+        int64_t nn2 = 0;
+        for (int64_t i = 0; i < nchg; ++i) {
+            int32_t v = chg[i];
+            for (int64_t e = rp[v]; e < rp[v + 1]; ++e)
+                if (!mark[ci[e]]) { mark[ci[e]] = 1; nxt[nn2++] = ci[e]; }
+        }
+        for (int64_t i = 0; i < nn2; ++i) mark[nxt[i]] = 0;
+        int32_t *t = act; act = nxt; nxt = t;
+        nact = nn2;
+    }
+    free(act); free(nxt); free(chg); free(newv); free(mark); free(cnt);
+    if (stats) memcpy(stats, st, sizeof(st));
+    return 0;
+}
+
+int oracle_nbrcore(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *core,
+                   int64_t *stats)
+{
+    return index2core_sync(n, rp, ci, core, stats, 0);
+}
+
+int oracle_cntcore(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *core,
+                   int64_t *stats)
+{
+    return index2core_sync(n, rp, ci, core, stats, 1);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -3,7 +3,10 @@
 Each mutant is one plausible slip (a wrong comparison, a dropped update, a
 wrong index) applied to a temporary copy of ``oracle/oracle.c``. The copy is
 compiled and loaded in a subprocess, which runs a small pin battery: the
-brute-force definition on random graphs, closed forms and the paper's G1.
+brute-force definition on random graphs, closed forms and the paper's G1,
+for every rendition (BZ, Alg. 2, 3, 4, 6, NbrCore, CntCore), plus the
+hand-counted step structure of GPP and the round counts of the Index2core
+renditions.
 The battery must pass on the unmodified source and fail on every mutant.
 """
 import os
@@ -38,6 +41,17 @@ MUTANTS = {
     "histo-no-increment": ("histo[rp[u] + y - 1] += 1;", ""),
     "histo-init-slot": ("histo[rp[v] + (du < dv ? du : dv) - 1] += 1;",
                         "histo[rp[v] + dv - 1] += 1;"),
+    # GPP (Alg. 3)
+    "gpp-strict-frontier": ("if (!rem[v] && deg[v] <= k) front[nf++] = (int32_t)v;",
+                            "if (!rem[v] && deg[v] < k) front[nf++] = (int32_t)v;"),
+    "gpp-no-rem-guard": ("if (!rem[ci[e]]) { deg[ci[e]]--; st[2]++; }", "{ deg[ci[e]]--; st[2]++; }"),
+    "gpp-k-skip": ("if (nf == 0) { k++; continue; }", "if (nf == 0) { k += 2; continue; }"),
+    # NbrCore / CntCore
+    "i2c-cnt-strict": ("c += (core[ci[e]] >= core[v]);", "c += (core[ci[e]] > core[v]);"),
+    "i2c-in-place": ("chg[nchg] = v;\n                newv[nchg++] = h;",
+                     "chg[nchg] = v;\n                newv[nchg++] = h;\n                core[v] = h;"),
+    "i2c-no-neighbours": ("if (!mark[ci[e]]) { mark[ci[e]] = 1; nxt[nn2++] = ci[e]; }",
+                          "if (!mark[v]) { mark[v] = 1; nxt[nn2++] = v; }"),
 }
 
 BATTERY = textwrap.dedent(r"""
@@ -60,6 +74,14 @@ BATTERY = textwrap.dedent(r"""
         }}
         h, st = oracle.histocore(rp, ci, check=True)
         got["histo"] = h
+        got["gpp"], gst = oracle.gpp(rp, ci)
+        jr = oracle.hindex_jacobi(rp, ci)[1]
+        for nm, fn in (("nbr", oracle.nbrcore), ("cnt", oracle.cntcore)):
+            got[nm], ist = fn(rp, ci)
+            if ist["rounds"] != jr or ist["frontier"] != st["frontier"] or ist["violations"]:
+                fails.append((tag, nm + "-rounds"))
+        if gst["scans"] != gst["steps"] + max(want + [0]):
+            fails.append((tag, "gpp-scans"))
         for k, v in got.items():
             if list(v) != list(want):
                 fails.append((tag, k))
@@ -86,6 +108,13 @@ BATTERY = textwrap.dedent(r"""
     p3 = gg.path_graph(3).numpy()
     if oracle.check(*p3, np.array([1, 3, 1], np.int32)) != {{"range": 1, "certificate": 0, "fixpoint": 0}}:
         fails.append(("P3", "check-range"))
+
+    # GPP on paths, counted by hand: ceil(n/2) steps, n - 2 (even n) or
+    # n - 1 (odd n) decrements
+    for pn in (4, 5, 8):
+        _, gst = oracle.gpp(*gg.path_graph(pn).numpy())
+        if (gst["steps"], gst["decrements"]) != ((pn + 1) // 2, pn - 2 if pn % 2 == 0 else pn - 1):
+            fails.append((f"P{{pn}}", "gpp-steps"))
 
     n, edges, want = load_g1()
     run("G1", n, edges, want)
