@@ -54,7 +54,21 @@ typedef struct CUstream_st *pico_stream_t;
 
 typedef enum {
     PICO_ALGO_PEELONE = 0,   /* Alg. 4, Sec. III-C */
-    PICO_ALGO_HISTOCORE = 1  /* Alg. 6, Sec. IV-B */
+    PICO_ALGO_HISTOCORE = 1, /* Alg. 6, Sec. IV-B */
+    /* The baselines of the paper's evaluation (Sec. V), for comparisons on the
+       same runtime; single-graph entry points only (pico_coreness and
+       pico_coreness_i64; the batched form and the server take methods 0 and
+       1). They return the same coreness. */
+    PICO_ALGO_GPP = 2,          /* General Parallel Peel, Alg. 3: separate residual
+                                   degree and removed flag, no dynamic frontier */
+    PICO_ALGO_PEEL_CAS = 3,     /* PeelOne with atomicSub_{>=k} as a compare-and-swap
+                                   loop, as Sec. III-B states it */
+    PICO_ALGO_PEEL_ADDBACK = 4, /* PeelOne with the atomicAdd method of Fig. 4a: an
+                                   overshooting decrement is added back at once */
+    PICO_ALGO_NBRCORE = 5,      /* NbrCore: neighbours of changed vertices recompute
+                                   HINDEX (Alg. 2) from scratch */
+    PICO_ALGO_CNTCORE = 6       /* CntCore, Alg. 5: only the vertices with cnt below
+                                   their estimate (Thm. 2) recompute HINDEX */
 } pico_algo;
 
 typedef enum {
@@ -219,6 +233,9 @@ typedef struct {
     int64_t scanned;     /* PeelOne: residual-list entries read, summed over scans */
     int64_t pulled;      /* HistoCore: arcs scanned by pull rounds of UpdateHisto */
     int64_t pull_rounds; /* HistoCore: rounds whose UpdateHisto pulled */
+    int64_t extra;       /* PeelOne and its variants: atomics beyond the successful
+                            decrements (overshoots; failed compare-and-swaps) */
+    int64_t active;      /* NbrCore, CntCore: sum over rounds of the active-set size */
     /* Device time (ns) and count per phase kind, measured by CTA 0 from one
        grid barrier to the next: [0] init, [1] PeelOne residual scan,
        [2..4] PeelOne frontier waves with < 64 work units / fewer units than

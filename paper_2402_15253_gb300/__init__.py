@@ -22,7 +22,17 @@ LIB_PATH = os.path.join(_HERE, "libpico.so")
 
 PICO_ALGO_PEELONE = 0
 PICO_ALGO_HISTOCORE = 1
+PICO_ALGO_GPP = 2
+PICO_ALGO_PEEL_CAS = 3
+PICO_ALGO_PEEL_ADDBACK = 4
+PICO_ALGO_NBRCORE = 5
+PICO_ALGO_CNTCORE = 6
 ALGOS = {"peelone": PICO_ALGO_PEELONE, "histocore": PICO_ALGO_HISTOCORE}
+# the comparison baselines of the paper's evaluation (single-graph calls only)
+BASELINES = {"gpp": PICO_ALGO_GPP, "peel_cas": PICO_ALGO_PEEL_CAS,
+             "peel_addback": PICO_ALGO_PEEL_ADDBACK, "nbrcore": PICO_ALGO_NBRCORE,
+             "cntcore": PICO_ALGO_CNTCORE}
+METHODS = {**ALGOS, **BASELINES}
 
 PICO_UPDATE_AUTO = 0
 PICO_UPDATE_PUSH = 1
@@ -55,7 +65,8 @@ TRACE_KINDS = PHASES + ("updatehisto_pull",)
 class pico_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "algo", "levels", "kmax", "subrounds", "scans", "rounds", "frontier", "barriers",
-        "arcs", "atomics", "slots", "blocks", "scanned", "pulled", "pull_rounds")] + [
+        "arcs", "atomics", "slots", "blocks", "scanned", "pulled", "pull_rounds", "extra",
+        "active")] + [
             ("phase_ns", ctypes.c_int64 * 8),
                                                   ("phase_count", ctypes.c_int64 * 8)]
 
@@ -313,8 +324,9 @@ def coreness(row_ptr: torch.Tensor, col_idx: torch.Tensor, algo="peelone",
              out: torch.Tensor | None = None, stream=None, check: bool = True) -> torch.Tensor:
     """Coreness of a CSR graph held in CUDA tensors (row_ptr int32 or int64,
     col_idx int32). Returns an int32 tensor on the same device. With
-    ``check`` the stream is synchronised and device-side errors raise."""
-    a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    ``check`` the stream is synchronised and device-side errors raise.
+    ``algo``: a name of METHODS (the two methods or a baseline) or its value."""
+    a = METHODS[algo] if isinstance(algo, str) else int(algo)
     if not (row_ptr.is_cuda and col_idx.is_cuda):
         raise ValueError("row_ptr and col_idx must be CUDA tensors")
     if col_idx.dtype != torch.int32 or row_ptr.dtype not in (torch.int32, torch.int64):

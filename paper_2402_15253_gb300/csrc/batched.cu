@@ -95,7 +95,8 @@ __device__ __forceinline__ void solve_graph(const BatchParams &bp, int g, Dom &d
         peel::Params<int> p{bp.rp + v0 + g, bp.ci + a0,    n,      bp.core + v0,
                             bp.res0 + v0,   bp.res1 + v0,  bp.qs + v0, chunks,
                             chunk_cap,      bp.ctl,        bp.tn};
-        peel::run(p, dom, s_tmp, st, clk, arcs, atomics);
+        unsigned long long extra = 0;
+        peel::run(p, dom, s_tmp, st, clk, arcs, atomics, extra);
     } else {
         histo::Params<int> p;
         p.rp = bp.rp + v0 + g;

@@ -98,12 +98,53 @@ pico::LaunchCfg cfg_of(const DeviceState *d)
 // scratch allocation of the compute entry points is reported as failed.
 bool fault_alloc() { return env_ll("PICO_FAULT_ALLOC", 0) > 0; }
 
+bool single_graph_algo(int algo) { return algo >= PICO_ALGO_PEELONE && algo <= PICO_ALGO_CNTCORE; }
+
+size_t single_ws_bytes(long long n, long long m, int algo)
+{
+    switch (algo) {
+    case PICO_ALGO_PEELONE:
+    case PICO_ALGO_PEEL_CAS:
+    case PICO_ALGO_PEEL_ADDBACK: return pico::peelone_ws_bytes(n, m);
+    case PICO_ALGO_HISTOCORE: return pico::histocore_ws_bytes(n, m);
+    case PICO_ALGO_GPP: return pico::gpp_ws_bytes(n, m);
+    case PICO_ALGO_NBRCORE:
+    case PICO_ALGO_CNTCORE: return pico::index2core_ws_bytes(n, m);
+    default: return 0;
+    }
+}
+
+template <typename Off>
+int launch_single(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_t *out, int algo,
+                  void *ws, pico::LastResult *last, cudaStream_t stream,
+                  const pico::LaunchCfg &cfg)
+{
+    switch (algo) {
+    case PICO_ALGO_PEELONE:
+        return pico::launch_peelone<Off>(rp, ci, n, m, out, ws, last, stream, cfg,
+                                         pico::kPeelRepair);
+    case PICO_ALGO_PEEL_CAS:
+        return pico::launch_peelone<Off>(rp, ci, n, m, out, ws, last, stream, cfg,
+                                         pico::kPeelCas);
+    case PICO_ALGO_PEEL_ADDBACK:
+        return pico::launch_peelone<Off>(rp, ci, n, m, out, ws, last, stream, cfg,
+                                         pico::kPeelAddBack);
+    case PICO_ALGO_HISTOCORE:
+        return pico::launch_histocore<Off>(rp, ci, n, m, out, ws, last, stream, cfg);
+    case PICO_ALGO_GPP: return pico::launch_gpp<Off>(rp, ci, n, m, out, ws, last, stream, cfg);
+    case PICO_ALGO_NBRCORE:
+    case PICO_ALGO_CNTCORE:
+        return pico::launch_index2core<Off>(rp, ci, n, m, out, ws, last, stream, cfg,
+                                            algo == PICO_ALGO_CNTCORE);
+    default: return -1;
+    }
+}
+
 template <typename Off>
 int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_t *out,
                   int algo, cudaStream_t stream)
 {
-    if (n < 0 || m < 0 || (algo != PICO_ALGO_PEELONE && algo != PICO_ALGO_HISTOCORE))
-        return PICO_ERR_INVALID_ARG;
+    if (n < 0 || m < 0 || !single_graph_algo(algo)) return PICO_ERR_INVALID_ARG;
     if (n == 0) return PICO_OK;
     if (!rp || !out || (m > 0 && !ci)) return PICO_ERR_INVALID_ARG;
     if (n >= INT32_MAX) return PICO_ERR_INVALID_ARG;
@@ -119,16 +160,13 @@ int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_
         }
         return PICO_OK;
     }
-    const size_t bytes = algo == PICO_ALGO_PEELONE ? pico::peelone_ws_bytes(n, m)
-                                                   : pico::histocore_ws_bytes(n, m);
+    const size_t bytes = single_ws_bytes(n, m, algo);
     void *ws = nullptr;
     if (fault_alloc() || cudaMallocAsync(&ws, bytes, stream) != cudaSuccess) {
         cudaGetLastError();
         return PICO_ERR_OOM;
     }
-    rc = algo == PICO_ALGO_PEELONE
-             ? pico::launch_peelone<Off>(rp, ci, n, m, out, ws, d->last, stream, cfg_of(d))
-             : pico::launch_histocore<Off>(rp, ci, n, m, out, ws, d->last, stream, cfg_of(d));
+    rc = launch_single<Off>(rp, ci, n, m, out, algo, ws, d->last, stream, cfg_of(d));
     cudaFreeAsync(ws, stream);
     if (rc != 0) {
         cudaGetLastError();
@@ -197,9 +235,7 @@ size_t pico_workspace_bytes_batched(int32_t G, int64_t total_vertices, int64_t t
 size_t pico_workspace_bytes(int64_t n, int64_t m, int algo)
 {
     if (n < 0 || m < 0) return 0;
-    if (algo == PICO_ALGO_PEELONE) return pico::peelone_ws_bytes(n, m);
-    if (algo == PICO_ALGO_HISTOCORE) return pico::histocore_ws_bytes(n, m);
-    return 0;
+    return single_ws_bytes(n, m, algo);
 }
 
 const char *pico_status_string(int status)
@@ -267,6 +303,8 @@ int pico_get_stats(pico_stream_t stream, pico_stats *out)
     out->scanned = (int64_t)h.stats[pico::kStScanned];
     out->pulled = (int64_t)h.stats[pico::kStPulled];
     out->pull_rounds = (int64_t)h.stats[pico::kStPullRounds];
+    out->extra = (int64_t)h.stats[pico::kStExtra];
+    out->active = (int64_t)h.stats[pico::kStActive];
     for (int i = 0; i < 8; ++i) {
         out->phase_ns[i] = (int64_t)h.stats[pico::kStPhaseNs + i];
         out->phase_count[i] = (int64_t)h.stats[pico::kStPhaseCount + i];

@@ -1,12 +1,13 @@
 // PeelOne (Sec. III, Alg. 4) on one graph as one persistent cooperative
 // kernel: the algorithm body is peel::run (peelone.cuh) over the whole grid.
 #include "peelone.cuh"
+#include "pico.h"
 #include "pico_launch.h"
 
 namespace pico {
 namespace {
 
-template <typename Off>
+template <typename Off, int Mode>
 __global__ void __launch_bounds__(kThreads, 2)
     peelone_kernel(peel::Params<Off> p, LastResult *last, unsigned long long limit_ns)
 {
@@ -16,7 +17,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ unsigned long long st[kStCount];   // statistics, written by thread 0
     if (threadIdx.x < kStCount) st[threadIdx.x] = 0;
     __syncthreads();
-    unsigned long long arcs = 0, atomics = 0;
+    unsigned long long arcs = 0, atomics = 0, extra = 0;
     PhaseClock clk;
     if (blockIdx.x == 0 && threadIdx.x == 0 && last->trace_on) {
         last->trace_len = 0;
@@ -25,11 +26,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     clk.start();
     GridDom dom{p.ctl, s_snap, limit_ns};
-    peel::run(p, dom, s_tmp, st, clk, arcs, atomics);
+    peel::run<Off, GridDom, Mode>(p, dom, s_tmp, st, clk, arcs, atomics, extra);
     block_sum_to(arcs, &p.ctl->stats[kStArcs], s_red);
     block_sum_to(atomics, &p.ctl->stats[kStAtomics], s_red);
+    block_sum_to(extra, &p.ctl->stats[kStExtra], s_red);
     if (blockIdx.x != 0 && threadIdx.x < kStCount) st[threadIdx.x] = 0;
-    finish_block(p.ctl, last, 0, st, kStCount);
+    finish_block(p.ctl, last,
+                 Mode == kPeelRepair ? PICO_ALGO_PEELONE
+                                     : (Mode == kPeelCas ? PICO_ALGO_PEEL_CAS : PICO_ALGO_PEEL_ADDBACK),
+                 st, kStCount);
 }
 
 }  // namespace
@@ -53,7 +58,7 @@ size_t peelone_ws_bytes(long long n, long long m)
 
 template <typename Off>
 int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *core, void *ws,
-                   LastResult *last, cudaStream_t stream, const LaunchCfg &cfg)
+                   LastResult *last, cudaStream_t stream, const LaunchCfg &cfg, int mode)
 {
     Carver c(ws);
     peel::Params<Off> p;
@@ -70,10 +75,14 @@ int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *
     p.tn = cfg.tn;
     if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
 
-    static int occ[64] = {};
-    int &o = occ[cfg.device & 63];
+    if (mode < kPeelRepair || mode > kPeelAddBack) return -1;
+    const void *fns[3] = {(const void *)peelone_kernel<Off, kPeelRepair>,
+                          (const void *)peelone_kernel<Off, kPeelCas>,
+                          (const void *)peelone_kernel<Off, kPeelAddBack>};
+    static int occ[3][64] = {};
+    int &o = occ[mode][cfg.device & 63];
     if (o == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, peelone_kernel<Off>, kThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[mode], kThreads, 0) !=
                 cudaSuccess ||
             o <= 0)
             return -3;
@@ -82,16 +91,15 @@ int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *
     dim3 grid(cfg.sms * per_sm), block(kThreads);
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&p, &last, &limit};
-    if (cudaLaunchCooperativeKernel((const void *)peelone_kernel<Off>, grid, block, args, 0,
-                                    stream) != cudaSuccess)
+    if (cudaLaunchCooperativeKernel(fns[mode], grid, block, args, 0, stream) != cudaSuccess)
         return -3;
     return 0;
 }
 
 template int launch_peelone<int>(const int *, const int *, long long, long long, int *, void *,
-                                 LastResult *, cudaStream_t, const LaunchCfg &);
+                                 LastResult *, cudaStream_t, const LaunchCfg &, int);
 template int launch_peelone<long long>(const long long *, const int *, long long, long long,
                                        int *, void *, LastResult *, cudaStream_t,
-                                       const LaunchCfg &);
+                                       const LaunchCfg &, int);
 
 }  // namespace pico

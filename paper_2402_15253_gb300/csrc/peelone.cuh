@@ -24,6 +24,15 @@
 //           give the same answer.
 // Every vertex is queued exactly once over the whole run (only one thread can
 // move it from k + 1 to k), so the queue is the peel order and needs n slots.
+//
+// Two other ways to keep a decrement from taking a vertex below k are built
+// for comparison (the ablation of Sec. V, Fig. 4): kPeelCas is the paper's
+// atomicSub_{>=k} as a compare-and-swap loop that never writes a value below
+// k (no repair needed); kPeelAddBack is the atomicAdd method of Fig. 4a, where
+// a thread whose decrement went below k adds the unit back at once. All three
+// give the same levels, waves and results; `extra` counts the atomics beyond
+// the successful decrements (overshoots repaired, failed compare-and-swaps,
+// or overshoot-plus-add-back pairs).
 #pragma once
 
 #include "pico_device.cuh"
@@ -50,7 +59,7 @@ struct Params {
     Tuning tn;
 };
 
-template <typename Off>
+template <typename Off, int Mode = kPeelRepair>
 struct Arc {
     static constexpr int kArcs = 4;
     const Off *rp;
@@ -63,7 +72,7 @@ struct Arc {
     int k;
     unsigned qs_cap;
     Tuning tn;
-    unsigned long long n_arcs = 0, n_atomics = 0;
+    unsigned long long n_arcs = 0, n_atomics = 0, n_extra = 0;
 
     __device__ __forceinline__ bool item(int, int &, int &) { return true; }
 
@@ -80,8 +89,35 @@ struct Arc {
             if (valid[j]) {
                 ++n_arcs;
                 if (c[j] > k) {
-                    old[j] = atomicSub(core + u[j], 1);
-                    ++n_atomics;
+                    if (Mode == kPeelCas) {   // atomicSub_{>=k}: never below k
+                        int cur = c[j];
+                        for (;;) {
+                            const int prev = atomicCAS(core + u[j], cur, cur - 1);
+                            ++n_atomics;
+                            if (prev == cur) {
+                                old[j] = cur;
+                                break;
+                            }
+                            ++n_extra;
+                            if (prev <= k) {   // another thread took u to k
+                                old[j] = prev;
+                                break;
+                            }
+                            cur = prev;
+                        }
+                    } else {
+                        old[j] = atomicSub(core + u[j], 1);
+                        ++n_atomics;
+                        if (old[j] <= k) {   // overshoot past k (a racing decrement)
+                            if (Mode == kPeelAddBack) {
+                                atomicAdd(core + u[j], 1);
+                                ++n_atomics;
+                                n_extra += 2;
+                            } else {
+                                ++n_extra;   // undone by the repair after the level
+                            }
+                        }
+                    }
                 }
             }
         }
@@ -116,9 +152,10 @@ __device__ __forceinline__ void repair(const Params<Off> &p, int k, unsigned s0,
 
 // PeelOne on one graph. Every thread of the domain calls it. st: per-CTA
 // statistics in shared memory (thread 0 writes); s_tmp: >= 128 shared words.
-template <typename Off, typename Dom>
+template <typename Off, typename Dom, int Mode = kPeelRepair>
 __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned long long *st,
-                    PhaseClock &clk, unsigned long long &arcs, unsigned long long &atomics)
+                    PhaseClock &clk, unsigned long long &arcs, unsigned long long &atomics,
+                    unsigned long long &extra)
 {
     Ctrl *ctl = p.ctl;
     unsigned *live = dom.live();
@@ -169,7 +206,8 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
             live[L_KEPT + (slot + 1) % 3] = 0;
             live[L_MIN + (slot + 1) % 3] = 0;
         }
-        if (prev_k >= 0) repair(p, prev_k, r_s0, r_e0, r_s1, r_e1, tid, nthreads);
+        if (Mode == kPeelRepair && prev_k >= 0)
+            repair(p, prev_k, r_s0, r_e0, r_s1, r_e1, tid, nthreads);
         prev_k = -1;
 
         // scan the residual list at level k (kScanItems vertices per thread)
@@ -240,11 +278,12 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
         unsigned s0 = qs0, s1 = qb0;
         while (s0 < e0 || s1 < e1) {
             const unsigned units = (e0 - s0 + 31) / 32 + (e1 - s1);
-            Arc<Off> f{p.rp, p.core, p.qs, p.qb, p.qb_cap, ctl, live, k, (unsigned)n, p.tn};
+            Arc<Off, Mode> f{p.rp, p.core, p.qs, p.qb, p.qb_cap, ctl, live, k, (unsigned)n, p.tn};
             expand(p.rp, p.ci, p.qs + s0, e0 - s0, p.qb + s1, e1 - s1, gwarp, nwarps, f, p.tn,
                    batch_width(e0 - s0, e1 - s1, nwarps));
             arcs += f.n_arcs;
             atomics += f.n_atomics;
+            extra += f.n_extra;
             if (!dom.sync()) return;
             if (threadIdx.x == 0) {
                 ++st[kStBarriers];
@@ -267,7 +306,8 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
         r_e1 = e1;
         k = k + 1;
     }
-    if (prev_k >= 0) repair(p, prev_k, r_s0, r_e0, r_s1, r_e1, tid, nthreads);
+    if (Mode == kPeelRepair && prev_k >= 0)
+        repair(p, prev_k, r_s0, r_e0, r_s1, r_e1, tid, nthreads);
 }
 
 }  // namespace peel

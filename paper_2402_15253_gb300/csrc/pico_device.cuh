@@ -40,6 +40,11 @@ constexpr int kPullPct = 40;                  // auto: pull when the changed ver
                                               // hold >= this % of the arcs ...
 constexpr long long kPullMinArcs = 1ll << 22;  // ... of a graph with at least this many
 
+// How PeelOne keeps a decrement from taking a vertex below the level k
+// (peelone.cuh): guard + repair after the level, compare-and-swap loop, or
+// add-back.
+enum : int { kPeelRepair = 0, kPeelCas = 1, kPeelAddBack = 2 };
+
 struct Tuning {
     int small_deg;
     int chunk;
@@ -67,7 +72,7 @@ struct alignas(128) Line {
 enum StatIdx : int {
     kStLevels = 0, kStKmax, kStSubrounds, kStScans, kStRounds, kStFrontier,
     kStBarriers, kStArcs, kStAtomics, kStSlots, kStBlocks, kStScanned, kStPulled,
-    kStPullRounds,
+    kStPullRounds, kStExtra, kStActive,
     kStPhaseNs = 16,      // 16..23: device time per phase kind (CTA 0's view)
     kStPhaseCount = 24,   // 24..31: phases per kind
     kStCount = 32

@@ -45,13 +45,28 @@ size_t chunk_capacity(long long m);
 size_t peelone_ws_bytes(long long n, long long m);
 size_t histocore_ws_bytes(long long n, long long m);
 
+// mode: kPeelRepair (PeelOne), kPeelCas or kPeelAddBack (ablations)
 template <typename Off>
 int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *core,
-                   void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
+                   void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg,
+                   int mode = 0);
 
 template <typename Off>
 int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int *core,
                      void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
+
+// the comparison baselines of Sec. V (ablation.cu)
+size_t gpp_ws_bytes(long long n, long long m);
+size_t index2core_ws_bytes(long long n, long long m);
+
+template <typename Off>
+int launch_gpp(const Off *rp, const int *ci, long long n, long long m, int *core, void *ws,
+               LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
+
+template <typename Off>
+int launch_index2core(const Off *rp, const int *ci, long long n, long long m, int *core,
+                      void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg,
+                      bool use_cnt);
 
 size_t batched_ws_bytes(int G, long long total_n, long long total_m, int algo);
 
