@@ -394,6 +394,59 @@ def method_bytes(algo: str, st: dict, n: int, arcs: int, w_r: int) -> int:
     return b_min + 4 * (arcs + n) + 4 * st["slots"] + 8 * update_arcs + 8 * updated
 
 
+# average speedups the paper reports over its 24 datasets (RTX 3090; Sec. V):
+# PeelOne over GPP, CntCore over NbrCore, HistoCore over CntCore
+PAPER_AVG_SPEEDUPS = {"peelone_vs_gpp": 1.9, "cntcore_vs_nbrcore": 1.8,
+                      "histocore_vs_cntcore": 8.0}
+
+
+def bench_baselines(pico, rp, ci, n, arcs, ref, tuned, method_ms, stream):
+    """The comparison baselines of Sec. V on the same graph (CUDA events, the
+    median of up to three runs after one warm-up; one run when a run takes
+    over two seconds). Each must return the same coreness as PeelOne."""
+    import torch
+    fn = pico.pico_coreness if rp.dtype == torch.int32 else pico.pico_coreness_i64
+    out = torch.empty(n, dtype=torch.int32, device=rp.device)
+    keep = ("levels", "subrounds", "scans", "rounds", "frontier", "active", "arcs",
+            "atomics", "extra")
+    res = {}
+    for name, algo in pico.BASELINES.items():
+        peel_like = name in ("gpp", "peel_cas", "peel_addback")
+        pico.pico_set_tuning(*tuned["peelone" if peel_like else "histocore"])
+        times = []
+        for i in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = fn(rp, ci, n, arcs, out, algo, stream)
+            e1.record(stream)
+            if rc != 0:
+                raise pico.PicoError(rc, name)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            if times[0] > 2000.0 and len(times) == 2:
+                break
+        st = pico.pico_last_device_status(stream)
+        if st != 0:
+            raise pico.PicoError(st, name)
+        if not torch.equal(out, ref):
+            raise AssertionError(f"{name} disagrees with PeelOne")
+        stats = pico.pico_get_stats(stream)
+        res[name] = {"ms": statistics.median(times[1:]),
+                     "stats": {k: stats[k] for k in keep if stats[k]}}
+    ms = {**{k: v["ms"] for k, v in res.items()}, **method_ms}
+    speedups = {
+        "peelone_vs_gpp": ms["gpp"] / ms["peelone"],
+        "peelone_vs_peel_cas": ms["peel_cas"] / ms["peelone"],
+        "peelone_vs_peel_addback": ms["peel_addback"] / ms["peelone"],
+        "cntcore_vs_nbrcore": ms["nbrcore"] / ms["cntcore"],
+        "histocore_vs_cntcore": ms["cntcore"] / ms["histocore"],
+        "histocore_vs_nbrcore": ms["nbrcore"] / ms["histocore"],
+    }
+    return {"runs": res, "speedups": speedups, "paper_average_speedups": PAPER_AVG_SPEEDUPS,
+            "note": "same graph, same runtime and tuning; GPP, NbrCore and CntCore as Alg. 3, "
+                    "Sec. V and Alg. 5 describe them"}
+
+
 def job_totals(local_ms: float, local_units: int, device=None):
     """Whole-job time and work over the ranks of the current process group
     (or this process alone): the slowest rank's time and the sum of the
@@ -464,6 +517,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-baselines", action="store_true",
+                    help="skip the comparison baselines of the paper's evaluation")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--tuning", default="auto",
                     help="'auto' (autotune each method on the graph) or S,C,T,K: small_deg, "
@@ -642,6 +697,10 @@ def main():
                 raise AssertionError("e2e result differs")
         del d_rp, d_ci
 
+    if rank == 0 and not args.no_baselines:
+        line["baselines"] = bench_baselines(pico, rp, ci, n, arcs, out["peelone"], tuned,
+                                            {a: statistics.median(v) for a, v in per.items()},
+                                            stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)
     if rank == 0 and args.serve_requests > 0:
