@@ -522,7 +522,8 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--tuning", default="auto",
                     help="'auto' (autotune each method on the graph) or S,C,T,K: small_deg, "
-                         "chunk, batched CTA threads, cluster log2 arcs, for both methods")
+                         "chunk, batched CTA threads, cluster log2 arcs, for both methods "
+                         "(or PeelOne's/HistoCore's, separated by '/')")
     ap.add_argument("--serve-requests", type=int, default=0,
                     help="requests of the served-form measurement (0: skip)")
     args = ap.parse_args()
@@ -564,8 +565,10 @@ def main():
     for a in ("peelone", "histocore"):
         if args.tuning == "auto":
             tuned[a], _ = autotune.tune_single(pico, rp, ci, a, reps=2, use_cache=False)
-        else:
-            tuned[a] = tuple(int(x) for x in args.tuning.split(","))
+        else:   # S,C,T,K for both methods, or PeelOne's/HistoCore's
+            parts = args.tuning.split("/")
+            tuned[a] = tuple(int(x) for x in parts[min(len(parts) - 1, 0 if a == "peelone" else 1)]
+                             .split(","))
             if not autotune.valid(tuned[a]):
                 raise SystemExit(f"invalid --tuning {args.tuning}")
 
