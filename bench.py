@@ -447,6 +447,30 @@ def bench_baselines(pico, rp, ci, n, arcs, ref, tuned, method_ms, stream):
                     "Sec. V and Alg. 5 describe them"}
 
 
+def bench_auto(pico, rp, ci, n, arcs, ref, stream, reps=3):
+    """PICO_ALGO_AUTO on the same graph: the method the selector ran and its
+    time (median of `reps` after one warm-up)."""
+    import torch
+    fn = pico.pico_coreness if rp.dtype == torch.int32 else pico.pico_coreness_i64
+    out = torch.empty(n, dtype=torch.int32, device=rp.device)
+    times = []
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = fn(rp, ci, n, arcs, out, pico.PICO_ALGO_AUTO, stream)
+        e1.record(stream)
+        if rc != 0:
+            raise pico.PicoError(rc, "auto")
+        e1.synchronize()
+        if i:
+            times.append(e0.elapsed_time(e1))
+    if pico.pico_last_device_status(stream) != 0 or not torch.equal(out, ref):
+        raise AssertionError("auto selection failed or disagrees with PeelOne")
+    chose = pico.pico_get_stats(stream)["algo"]
+    return {"ms": statistics.median(times),
+            "method": {v: k for k, v in pico.ALGOS.items()}[chose]}
+
+
 def job_totals(local_ms: float, local_units: int, device=None):
     """Whole-job time and work over the ranks of the current process group
     (or this process alone): the slowest rank's time and the sum of the
@@ -700,6 +724,9 @@ def main():
                 raise AssertionError("e2e result differs")
         del d_rp, d_ci
 
+    if rank == 0:
+        pico.pico_set_tuning(*tuned["peelone"])
+        line["auto"] = bench_auto(pico, rp, ci, n, arcs, out["peelone"], stream)
     if rank == 0 and not args.no_baselines:
         line["baselines"] = bench_baselines(pico, rp, ci, n, arcs, out["peelone"], tuned,
                                             {a: statistics.median(v) for a, v in per.items()},

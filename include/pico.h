@@ -67,8 +67,17 @@ typedef enum {
                                    overshooting decrement is added back at once */
     PICO_ALGO_NBRCORE = 5,      /* NbrCore: neighbours of changed vertices recompute
                                    HINDEX (Alg. 2) from scratch */
-    PICO_ALGO_CNTCORE = 6       /* CntCore, Alg. 5: only the vertices with cnt below
+    PICO_ALGO_CNTCORE = 6,      /* CntCore, Alg. 5: only the vertices with cnt below
                                    their estimate (Thm. 2) recompute HINDEX */
+    /* Either method, chosen per graph (no counterpart in the paper, which
+       leaves the choice open). Single-graph calls decide on the device from
+       n, m and the largest degree: HistoCore when the degrees are skewed
+       (d_max >= 64 m/n) and m^2 <= 2^14 d_max n, PeelOne otherwise (a rule
+       fitted to GB300 timings of both methods). The batched form and the
+       server run PeelOne for every graph, which was faster than HistoCore on
+       every measured graph class in one-CTA and one-cluster domains.
+       pico_get_stats reports the method that ran. */
+    PICO_ALGO_AUTO = 7
 } pico_algo;
 
 typedef enum {
@@ -164,7 +173,7 @@ typedef struct pico_server pico_server;
 
 typedef struct {
     size_t hbm_budget_bytes; /* device bytes the admitted requests may hold */
-    int algo;                /* pico_algo used for every request */
+    int algo;                /* PICO_ALGO_PEELONE, _HISTOCORE or _AUTO for every request */
     int streams;             /* micro-batches in flight at once (1..64) */
     int max_batch;           /* requests per micro-batch (>= 1) */
     int single_graph;        /* 1: one single-graph call per request */

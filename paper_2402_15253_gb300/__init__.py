@@ -27,7 +27,8 @@ PICO_ALGO_PEEL_CAS = 3
 PICO_ALGO_PEEL_ADDBACK = 4
 PICO_ALGO_NBRCORE = 5
 PICO_ALGO_CNTCORE = 6
-ALGOS = {"peelone": PICO_ALGO_PEELONE, "histocore": PICO_ALGO_HISTOCORE}
+PICO_ALGO_AUTO = 7
+ALGOS = {"peelone": PICO_ALGO_PEELONE, "histocore": PICO_ALGO_HISTOCORE, "auto": PICO_ALGO_AUTO}
 # the comparison baselines of the paper's evaluation (single-graph calls only)
 BASELINES = {"gpp": PICO_ALGO_GPP, "peel_cas": PICO_ALGO_PEEL_CAS,
              "peel_addback": PICO_ALGO_PEEL_ADDBACK, "nbrcore": PICO_ALGO_NBRCORE,

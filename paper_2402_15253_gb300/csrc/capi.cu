@@ -98,7 +98,7 @@ pico::LaunchCfg cfg_of(const DeviceState *d)
 // scratch allocation of the compute entry points is reported as failed.
 bool fault_alloc() { return env_ll("PICO_FAULT_ALLOC", 0) > 0; }
 
-bool single_graph_algo(int algo) { return algo >= PICO_ALGO_PEELONE && algo <= PICO_ALGO_CNTCORE; }
+bool single_graph_algo(int algo) { return algo >= PICO_ALGO_PEELONE && algo <= PICO_ALGO_AUTO; }
 
 size_t single_ws_bytes(long long n, long long m, int algo)
 {
@@ -110,6 +110,7 @@ size_t single_ws_bytes(long long n, long long m, int algo)
     case PICO_ALGO_GPP: return pico::gpp_ws_bytes(n, m);
     case PICO_ALGO_NBRCORE:
     case PICO_ALGO_CNTCORE: return pico::index2core_ws_bytes(n, m);
+    case PICO_ALGO_AUTO: return pico::hybrid_ws_bytes(n, m);
     default: return 0;
     }
 }
@@ -132,6 +133,7 @@ int launch_single(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_
     case PICO_ALGO_HISTOCORE:
         return pico::launch_histocore<Off>(rp, ci, n, m, out, ws, last, stream, cfg);
     case PICO_ALGO_GPP: return pico::launch_gpp<Off>(rp, ci, n, m, out, ws, last, stream, cfg);
+    case PICO_ALGO_AUTO: return pico::launch_hybrid<Off>(rp, ci, n, m, out, ws, last, stream, cfg);
     case PICO_ALGO_NBRCORE:
     case PICO_ALGO_CNTCORE:
         return pico::launch_index2core<Off>(rp, ci, n, m, out, ws, last, stream, cfg,
@@ -197,6 +199,7 @@ int pico_coreness_batched(const int64_t *vtx_off, const int64_t *arc_off, int32_
                           int64_t total_vertices, int64_t total_arcs, int32_t *out_core,
                           int algo, pico_stream_t stream)
 {
+    if (algo == PICO_ALGO_AUTO) algo = PICO_ALGO_PEELONE;   // faster on every measured class
     if (G < 0 || total_vertices < 0 || total_arcs < 0 ||
         (algo != PICO_ALGO_PEELONE && algo != PICO_ALGO_HISTOCORE))
         return PICO_ERR_INVALID_ARG;
@@ -228,6 +231,7 @@ size_t pico_workspace_bytes_batched(int32_t G, int64_t total_vertices, int64_t t
                                     int algo)
 {
     if (G < 0 || total_vertices < 0 || total_arcs < 0) return 0;
+    if (algo == PICO_ALGO_AUTO) algo = PICO_ALGO_PEELONE;
     if (algo != PICO_ALGO_PEELONE && algo != PICO_ALGO_HISTOCORE) return 0;
     return pico::batched_ws_bytes(G, total_vertices, total_arcs, algo);
 }

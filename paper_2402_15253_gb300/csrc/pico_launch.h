@@ -68,6 +68,13 @@ int launch_index2core(const Off *rp, const int *ci, long long n, long long m, in
                       void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg,
                       bool use_cnt);
 
+// method selection per graph (hybrid.cu)
+size_t hybrid_ws_bytes(long long n, long long m);
+
+template <typename Off>
+int launch_hybrid(const Off *rp, const int *ci, long long n, long long m, int *core, void *ws,
+                  LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
+
 size_t batched_ws_bytes(int G, long long total_n, long long total_m, int algo);
 
 int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const int32_t *rp,

@@ -252,7 +252,8 @@ int64_t pico_clock_ns(void) { return now_ns(); }
 pico_server *pico_server_create(const pico_server_config *cfg)
 {
     if (!cfg || cfg->streams < 1 || cfg->streams > 64 || cfg->max_batch < 1 ||
-        (cfg->algo != PICO_ALGO_PEELONE && cfg->algo != PICO_ALGO_HISTOCORE))
+        (cfg->algo != PICO_ALGO_PEELONE && cfg->algo != PICO_ALGO_HISTOCORE &&
+         cfg->algo != PICO_ALGO_AUTO))
         return nullptr;
     pico_server *s = new pico_server();
     s->cfg = *cfg;

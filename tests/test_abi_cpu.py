@@ -62,8 +62,9 @@ def test_argument_checks_need_no_gpu(lib):
     # negative sizes, unknown method, null pointers: rejected before any CUDA call
     assert L.pico_coreness(vp(None), vp(None), ctypes.c_int64(-1), ctypes.c_int64(0), vp(None),
                            0, vp(None)) == pico.PICO_ERR_INVALID_ARG
-    assert L.pico_coreness(vp(8), vp(8), ctypes.c_int64(4), ctypes.c_int64(4), vp(8),
-                           7, vp(None)) == pico.PICO_ERR_INVALID_ARG
+    for bad_algo in (-1, 8, 99):
+        assert L.pico_coreness(vp(8), vp(8), ctypes.c_int64(4), ctypes.c_int64(4), vp(8),
+                               bad_algo, vp(None)) == pico.PICO_ERR_INVALID_ARG
     assert L.pico_coreness(vp(None), vp(8), ctypes.c_int64(4), ctypes.c_int64(4), vp(8),
                            0, vp(None)) == pico.PICO_ERR_INVALID_ARG
     assert L.pico_coreness_i64(vp(8), vp(8), ctypes.c_int64(1 << 31), ctypes.c_int64(4), vp(8),
