@@ -87,7 +87,8 @@ enum PhaseKind : int {
 
 
 struct Ctrl {
-    Line bar;                 // w[0] arrivals, w[1] generation
+    Line bar;                 // w[0..1]: arrivals at grid barriers (64-bit, whole launch)
+    Line gen;                 // w[0]: grid barriers completed
     Line stat;                // w[0] status, w[1] CTAs that finished
     Line live;                // counters updated with atomics
     Line snap[2];             // live counters as of the last barrier (by parity)
@@ -194,38 +195,42 @@ __device__ __forceinline__ int status_of(Ctrl *c)
 // ---------------------------------------------------------------------------
 // s_snap: shared memory, kLiveWords + 1 words; after the call s_snap[i] holds
 // the live counter i as of the barrier and s_snap[kLiveWords] the status.
-// Warp 0 of each CTA takes part: lane 0 arrives and waits, and the snapshot
-// is copied and read with one word per lane (a single memory round trip).
-static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap, unsigned long long limit_ns)
+// gen: barriers this CTA has completed in the launch (the same in every CTA).
+// Thread 0 of each CTA takes part. Arrivals count up over the whole launch
+// (a 64-bit counter, never reset), so barrier number gen is complete when
+// (gen + 1) x gridDim.x CTAs have arrived. The arrival is one acquire-release
+// atomic (it publishes the CTA's counter updates, ordered before it by the
+// CTA barrier, and lets the last arrival see everyone's). The last arrival
+// copies the live counters into the snapshot of the barrier's parity with
+// vector loads and stores and releases the generation word; the others wait
+// for that word with acquire loads (bounded: limit_ns and the status word)
+// and read the snapshot. A snapshot of parity p is rewritten two barriers
+// later, which every reader must reach first.
+static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap,
+                                              unsigned long long limit_ns, unsigned gen)
 {
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const unsigned lane = threadIdx.x;
-        unsigned gen = 0, prev = 0;
-        if (lane == 0) {
-            gen = ld_acquire(&c->bar.w[1]);
-            __threadfence();
-            prev = atomicAdd(&c->bar.w[0], 1u);
-        }
-        gen = __shfl_sync(kFull, gen, 0);
-        prev = __shfl_sync(kFull, prev, 0);
+    if (threadIdx.x == 0) {
         const unsigned par = (gen + 1) & 1;
-        if (prev == gridDim.x - 1) {
-            // last arrival: every lane synchronises with the other CTAs'
-            // arrivals before reading the counters they updated
-            (void)ld_acquire(&c->bar.w[0]);
-            c->snap[par].w[lane] = ld_relaxed(&c->live.w[lane]);
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) {
-                atomicExch(&c->bar.w[0], 0u);
-                __threadfence();
-                st_release(&c->bar.w[1], gen + 1);
-            }
-        } else if (lane == 0) {
+        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        unsigned long long old;
+        asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;"
+                     : "=l"(old)
+                     : "l"(reinterpret_cast<unsigned long long *>(c->bar.w))
+                     : "memory");
+        uint4 *snap = reinterpret_cast<uint4 *>(c->snap[par].w);
+        if (old + 1 == target) {
+            const uint4 *live = reinterpret_cast<const uint4 *>(c->live.w);
+            uint4 t[kLiveWords / 4];
+#pragma unroll
+            for (int i = 0; i < kLiveWords / 4; ++i) t[i] = __ldcg(live + i);
+#pragma unroll
+            for (int i = 0; i < kLiveWords / 4; ++i) __stcg(snap + i, t[i]);
+            st_release(&c->gen.w[0], gen + 1);
+        } else {
             const unsigned long long t0 = gtime();
             unsigned spins = 0;
-            while (ld_acquire(&c->bar.w[1]) == gen) {
+            while (ld_acquire(&c->gen.w[0]) == gen) {
                 if ((++spins & 63) == 0) {
                     if (status_of(c) != 0) break;
                     if (gtime() - t0 > limit_ns) {
@@ -235,10 +240,15 @@ static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap, unsigne
                 }
             }
         }
-        __syncwarp();
-        (void)ld_acquire(&c->bar.w[1]);   // every lane acquires the release
-        s_snap[lane] = ld_relaxed(c->snap[par].w + lane);
-        if (lane == 0) s_snap[kLiveWords] = (unsigned)status_of(c);
+#pragma unroll
+        for (int i = 0; i < kLiveWords / 4; ++i) {
+            const uint4 t = __ldcg(snap + i);
+            s_snap[4 * i] = t.x;
+            s_snap[4 * i + 1] = t.y;
+            s_snap[4 * i + 2] = t.z;
+            s_snap[4 * i + 3] = t.w;
+        }
+        s_snap[kLiveWords] = (unsigned)status_of(c);
     }
     __syncthreads();
     return s_snap[kLiveWords] == 0;
@@ -687,9 +697,10 @@ struct GridDom {
     Ctrl *ctl;
     unsigned *s_snap;
     unsigned long long limit_ns;
+    unsigned gen = 0;   // barriers passed (the same in every thread of the launch)
     static constexpr bool kGrid = true;
     __device__ __forceinline__ unsigned *live() const { return ctl->live.w; }
-    __device__ __forceinline__ bool sync() { return grid_sync(ctl, s_snap, limit_ns); }
+    __device__ __forceinline__ bool sync() { return grid_sync(ctl, s_snap, limit_ns, gen++); }
     __device__ __forceinline__ unsigned tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ __forceinline__ unsigned nthreads() const { return gridDim.x * blockDim.x; }
     __device__ __forceinline__ unsigned cta() const { return blockIdx.x; }

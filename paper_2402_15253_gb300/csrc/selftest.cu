@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256) wait_timeout_kernel(Ctrl *ctl, LastResult
     __shared__ unsigned long long st[kStCount];
     if (threadIdx.x < kStCount) st[threadIdx.x] = 0;
     __syncthreads();
-    if (blockIdx.x != 0) grid_sync(ctl, s_snap, limit_ns);   // CTA 0 never arrives
+    if (blockIdx.x != 0) grid_sync(ctl, s_snap, limit_ns, 0);   // CTA 0 never arrives
     finish_block(ctl, last, -1, st, kStCount);
 }
 
