@@ -293,6 +293,47 @@ int pico_selftest_wait_timeout(int limit_ms, pico_stream_t stream);
 int pico_set_tuning(int small_deg, int chunk, int batched_threads, int cluster_log2);
 int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads, int *cluster_log2);
 
+/*
+ * Core maintenance (no counterpart in the paper, which lists it among the
+ * uses of the Index2core paradigm): a graph and its coreness kept on the
+ * device and brought up to date after each batch of edge insertions and
+ * deletions, without recomputation from the degrees.
+ *
+ * pico_dyn_create copies the CSR (row_ptr int64, n + 1 entries; col_idx m
+ * arcs; device memory, read only) into the state, which holds room for
+ * capacity_arcs arcs (>= m), computes its coreness and synchronises `stream`.
+ * Returns NULL for invalid arguments (n < 1, capacity below m) or failure.
+ *
+ * pico_dyn_update applies one batch of undirected edges: ins and del are
+ * device arrays of n_ins and n_del pairs (u, v) (int32, 2 entries per edge).
+ * Every deleted edge must be in the graph and every inserted edge must not;
+ * no self-loops, no edge twice in a batch. Deletions are applied first. The
+ * call synchronises `stream` and returns PICO_OK, PICO_ERR_BAD_GRAPH for a
+ * batch that breaks these rules (the state is then unchanged),
+ * PICO_ERR_INVALID_ARG (bad sizes, too little capacity) or a device status.
+ * After an update with insertions, pico_get_stats describes the insertion
+ * passes (algo PICO_STATS_MAINTENANCE: rounds = passes that raised a vertex,
+ * frontier = vertices raised, active = candidates); otherwise the NbrCore
+ * rounds of the deletions.
+ *
+ * pico_dyn_coreness copies the current coreness (n int32) to device memory;
+ * pico_dyn_graph exposes the current CSR (device pointers owned by the state,
+ * valid until the next update) and pico_dyn_copy_graph copies it out.
+ */
+#define PICO_STATS_MAINTENANCE 100
+typedef struct pico_dyn pico_dyn;
+pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                          int64_t capacity_arcs, pico_stream_t stream);
+int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_t *del,
+                    int64_t n_del, pico_stream_t stream);
+int pico_dyn_coreness(pico_dyn *d, int32_t *out_core, pico_stream_t stream);
+int pico_dyn_graph(pico_dyn *d, const int64_t **row_ptr, const int32_t **col_idx, int64_t *n,
+                   int64_t *m);
+/* Copies the current CSR into caller buffers (device memory: n + 1 int64 and
+   m int32, sizes from pico_dyn_graph), enqueued on `stream`. */
+int pico_dyn_copy_graph(pico_dyn *d, int64_t *row_ptr, int32_t *col_idx, pico_stream_t stream);
+void pico_dyn_destroy(pico_dyn *d);
+
 /* Direction of HistoCore's UpdateHisto (Sec. IV-B, Alg. 6). */
 #define PICO_UPDATE_AUTO 0   /* per round: pull when the round's changed vertices hold at
                                 least pull_pct % of the arcs of a graph with >= 2^22 arcs */

@@ -128,6 +128,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_set_tuning.restype = i32
     L.pico_get_tuning.argtypes = [vp, vp, vp, vp]
     L.pico_get_tuning.restype = i32
+    L.pico_dyn_create.argtypes = [vp, vp, i64, i64, i64, vp]
+    L.pico_dyn_create.restype = vp
+    L.pico_dyn_update.argtypes = [vp, vp, i64, vp, i64, vp]
+    L.pico_dyn_update.restype = i32
+    L.pico_dyn_coreness.argtypes = [vp, vp, vp]
+    L.pico_dyn_coreness.restype = i32
+    L.pico_dyn_graph.argtypes = [vp, vp, vp, vp, vp]
+    L.pico_dyn_graph.restype = i32
+    L.pico_dyn_copy_graph.argtypes = [vp, vp, vp, vp]
+    L.pico_dyn_copy_graph.restype = i32
+    L.pico_dyn_destroy.argtypes = [vp]
+    L.pico_dyn_destroy.restype = None
     L.pico_set_histo_update.argtypes = [i32, i32]
     L.pico_set_histo_update.restype = i32
     L.pico_get_histo_update.argtypes = [vp, vp]
@@ -254,6 +266,108 @@ def pico_get_trace(stream=None, cap: int = 8192) -> list:
         raise PicoError(k, "pico_get_trace")
     b = buf[:3 * k].view(-1, 3).tolist()
     return [(TRACE_KINDS[kind], units, ns / 1e6) for kind, units, ns in b]
+
+
+PICO_STATS_MAINTENANCE = 100
+
+
+def pico_dyn_create(row_ptr: torch.Tensor, col_idx: torch.Tensor, n: int, m: int,
+                    capacity_arcs: int, stream=None):
+    return load().pico_dyn_create(_ptr(row_ptr), _ptr(col_idx), n, m, capacity_arcs,
+                                  _stream(stream))
+
+
+def pico_dyn_update(d, ins: torch.Tensor | None, n_ins: int, dele: torch.Tensor | None,
+                    n_del: int, stream=None) -> int:
+    return load().pico_dyn_update(d, _ptr(ins) if ins is not None else None, n_ins,
+                                  _ptr(dele) if dele is not None else None, n_del, _stream(stream))
+
+
+def pico_dyn_coreness(d, out: torch.Tensor, stream=None) -> int:
+    return load().pico_dyn_coreness(d, _ptr(out), _stream(stream))
+
+
+def pico_dyn_graph(d):
+    rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
+    n, m = ctypes.c_int64(), ctypes.c_int64()
+    rc = load().pico_dyn_graph(d, ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(n),
+                               ctypes.byref(m))
+    if rc != PICO_OK:
+        raise PicoError(rc, "pico_dyn_graph")
+    return rp.value, ci.value, n.value, m.value
+
+
+def pico_dyn_copy_graph(d, row_ptr: torch.Tensor, col_idx: torch.Tensor, stream=None) -> int:
+    return load().pico_dyn_copy_graph(d, _ptr(row_ptr), _ptr(col_idx), _stream(stream))
+
+
+def pico_dyn_destroy(d) -> None:
+    load().pico_dyn_destroy(d)
+
+
+class DynamicGraph:
+    """A graph and its coreness kept on the device under batches of edge
+    insertions and deletions (pico_dyn_*). ``row_ptr``/``col_idx``: CUDA
+    tensors of a CSR; ``capacity_arcs``: room for insertions (arcs)."""
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, capacity_arcs: int | None = None,
+                 stream=None):
+        self.device = row_ptr.device
+        rp = row_ptr.to(torch.int64).contiguous()
+        ci = col_idx.to(torch.int32).contiguous()
+        self.n = rp.numel() - 1
+        m = ci.numel()
+        cap = capacity_arcs if capacity_arcs is not None else max(2 * m, 1024)
+        with torch.cuda.device(self.device):
+            self._d = pico_dyn_create(rp, ci, self.n, m, cap, stream)
+        if not self._d:
+            raise PicoError(PICO_ERR_INVALID_ARG, "pico_dyn_create")
+
+    def update(self, insert=None, delete=None, stream=None) -> None:
+        """insert / delete: int32 CUDA tensors of shape (k, 2), undirected edges."""
+        def prep(e):
+            if e is None or len(e) == 0:
+                return None, 0
+            e = torch.as_tensor(e, dtype=torch.int32, device=self.device).contiguous()
+            return e, e.shape[0]
+        ins, ni = prep(insert)
+        dele, nd = prep(delete)
+        with torch.cuda.device(self.device):
+            rc = pico_dyn_update(self._d, ins, ni, dele, nd, stream)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_dyn_update")
+
+    def coreness(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        with torch.cuda.device(self.device):
+            rc = pico_dyn_coreness(self._d, out, stream)
+            if rc != PICO_OK:
+                raise PicoError(rc, "pico_dyn_coreness")
+            torch.cuda.current_stream().synchronize()
+        return out
+
+    def csr(self):
+        """Copies of the current row_ptr (int64) and col_idx (int32)."""
+        _, _, n, m = pico_dyn_graph(self._d)
+        rp = torch.empty(n + 1, dtype=torch.int64, device=self.device)
+        ci = torch.empty(max(m, 1), dtype=torch.int32, device=self.device)
+        with torch.cuda.device(self.device):
+            rc = pico_dyn_copy_graph(self._d, rp, ci)
+            if rc != PICO_OK:
+                raise PicoError(rc, "pico_dyn_copy_graph")
+            torch.cuda.current_stream().synchronize()
+        return rp, ci[:m]
+
+    def close(self) -> None:
+        if getattr(self, "_d", None):
+            pico_dyn_destroy(self._d)
+            self._d = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 PULL_PCT_DEFAULT = 40

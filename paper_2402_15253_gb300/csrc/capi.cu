@@ -179,6 +179,18 @@ int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_
 
 }  // namespace
 
+namespace pico {
+int current_device(LaunchCfg *cfg, LastResult **last)
+{
+    DeviceState *d = nullptr;
+    const int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    *cfg = cfg_of(d);
+    *last = d->last;
+    return PICO_OK;
+}
+}  // namespace pico
+
 extern "C" {
 
 int pico_coreness(const int32_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,

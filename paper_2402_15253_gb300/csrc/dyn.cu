@@ -1,0 +1,888 @@
+// Core maintenance: the coreness of a graph kept up to date under batches of
+// edge insertions and deletions, without recomputing it from the degrees.
+// The paper lists core maintenance among the uses of Index2core (Sec. I,
+// related work in Sec. VI); this is the path built on this library's kernels.
+//
+// A batch is applied in three steps, all on the device:
+//   1. The CSR is rebuilt: new degrees, an exclusive scan for the offsets,
+//      the surviving arcs copied row by row (a deleted arc is found in a hash
+//      set of the batch's deleted arcs), the inserted arcs appended.
+//   2. Deletions: coreness can only fall. The old coreness (capped at the new
+//      degree) is an upper bound, so the synchronous h-index iteration of
+//      Alg. 2, started from it with the deleted edges' endpoints as the first
+//      active set (the NbrCore rounds of ablation.cuh), converges to the new
+//      coreness: every fixpoint of HINDEX lies below the coreness, and the
+//      iteration never goes below it.
+//   3. Insertions: coreness can only rise; the value after step 2 is a lower
+//      bound. A pass tries to raise every vertex by one: the candidates are
+//      the vertices w with at least core(w) + 1 neighbours of core >= core(w);
+//      each counts its support (neighbours of higher core, or of equal core
+//      that are candidates) and candidates whose support falls below
+//      core(w) + 1 are peeled, which lowers their equal-core candidate
+//      neighbours' support, wave by wave as in PeelOne's dynamic frontier.
+//      The survivors of level K together with the vertices of core > K have
+//      minimum degree K + 1, so they lie in the (K + 1)-core and rise by one.
+//      Passes repeat until one raises nothing. Then no vertex is below its
+//      coreness: for the smallest k with a vertex below k in the true
+//      k-core X, those vertices all have core k - 1, are candidates, and keep
+//      a support of at least k from X through every peel, so they would rise.
+#include <algorithm>
+#include <cstring>
+
+#include "ablation.cuh"
+#include "pico.h"
+#include "pico_launch.h"
+
+namespace pico {
+namespace dyn {
+
+// ---------------------------------------------------------------------------
+// arc hash sets (open addressing, linear probing; 0 marks an empty slot)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long arc_key(int u, int v)
+{
+    return ((unsigned long long)(unsigned)u << 32 | (unsigned)v) + 1ull;
+}
+
+// slot of a key: the 64-bit finaliser of MurmurHash3 (Appleby), then the mask
+__device__ __forceinline__ unsigned hash_slot(unsigned long long k, unsigned mask)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (unsigned)k & mask;
+}
+
+// false if the key was already present (or the table is full)
+__device__ __forceinline__ bool set_insert(unsigned long long *tab, unsigned mask,
+                                           unsigned long long k)
+{
+    unsigned s = hash_slot(k, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe, s = (s + 1) & mask) {
+        const unsigned long long prev = atomicCAS(tab + s, 0ull, k);
+        if (prev == 0ull) return true;
+        if (prev == k) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool set_has(const unsigned long long *tab, unsigned mask,
+                                        unsigned long long k)
+{
+    unsigned s = hash_slot(k, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe, s = (s + 1) & mask) {
+        const unsigned long long x = __ldcg(tab + s);
+        if (x == k) return true;
+        if (x == 0ull) return false;
+    }
+    return false;
+}
+
+// batch errors (first one wins)
+enum : int { kBadId = 1, kDupInBatch = 2, kMissingArc = 3, kExistingArc = 4, kNegDegree = 5 };
+
+__device__ __forceinline__ void fail(int *err, int code) { atomicCAS(err, 0, code); }
+
+// ---------------------------------------------------------------------------
+// step 1: CSR rebuild
+// ---------------------------------------------------------------------------
+// Per-vertex insert/delete counts, touched flags and the two arc sets.
+__global__ void count_kernel(const int *ins, long long n_ins, const int *del, long long n_del,
+                             long long n, int *ins_cnt, int *del_cnt, unsigned char *touched,
+                             unsigned long long *instab, unsigned insmask,
+                             unsigned long long *deltab, unsigned delmask, int *err)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_ins + n_del;
+         i += stride) {
+        const bool is_ins = i < n_ins;
+        const int *e = is_ins ? ins + 2 * i : del + 2 * (i - n_ins);
+        const int u = e[0], v = e[1];
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v) {
+            fail(err, kBadId);
+            continue;
+        }
+        unsigned long long *tab = is_ins ? instab : deltab;
+        const unsigned mask = is_ins ? insmask : delmask;
+        if (!set_insert(tab, mask, arc_key(u, v)) || !set_insert(tab, mask, arc_key(v, u))) {
+            fail(err, kDupInBatch);
+            continue;
+        }
+        int *cnt = is_ins ? ins_cnt : del_cnt;
+        atomicAdd(cnt + u, 1);
+        atomicAdd(cnt + v, 1);
+        const unsigned char bit = is_ins ? 1 : 2;
+        atomicOr(reinterpret_cast<unsigned *>(touched + (u & ~3)), (unsigned)bit << (8 * (u & 3)));
+        atomicOr(reinterpret_cast<unsigned *>(touched + (v & ~3)), (unsigned)bit << (8 * (v & 3)));
+    }
+}
+
+// new degree of every vertex (into new_rp[v + 1], scanned in place afterwards)
+__global__ void degree_kernel(const long long *rp, long long n, const int *ins_cnt,
+                              const int *del_cnt, long long *new_rp, int *err)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const long long d = rp[v + 1] - rp[v] + ins_cnt[v] - del_cnt[v];
+        if (d < 0) fail(err, kNegDegree);
+        new_rp[v + 1] = d < 0 ? 0 : d;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) new_rp[0] = 0;
+}
+
+// In-place inclusive scan of a[1..n] by one persistent cooperative grid: each
+// CTA sums its contiguous range, CTA sums are scanned after a grid barrier,
+// then each CTA scans its range on top of its offset.
+__global__ void __launch_bounds__(kThreads) scan_kernel(long long *a, long long n, Ctrl *ctl,
+                                                         long long *cta_sum,
+                                                         unsigned long long limit_ns)
+{
+    __shared__ unsigned s_snap[kLiveWords + 1];
+    __shared__ long long s_w[kThreads / 32];
+    __shared__ long long s_carry;
+    GridDom dom{ctl, s_snap, limit_ns};
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = 1 + (long long)blockIdx.x * per;
+    const long long hi = lo + per < n + 1 ? lo + per : n + 1;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long mine = 0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) mine += a[i];
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
+    if (lane == 0) s_w[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (unsigned w = 0; w < nw; ++w) t += s_w[w];
+        cta_sum[blockIdx.x] = t;
+    }
+    if (!dom.sync()) return;
+    if (threadIdx.x == 0) {
+        long long off = 0;
+        for (unsigned b = 0; b < blockIdx.x; ++b) off += __ldcg(cta_sum + b);
+        s_carry = off;
+    }
+    __syncthreads();
+    for (long long base = lo; base < hi; base += blockDim.x) {
+        const long long i = base + threadIdx.x;
+        long long x = i < hi ? a[i] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(kFull, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            long long w = lane < nw ? s_w[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(kFull, w, o);
+                if ((int)lane >= o) w += y;
+            }
+            if (lane < nw) s_w[lane] = w;
+        }
+        __syncthreads();
+        const long long before = (warp ? s_w[warp - 1] : 0) + s_carry;
+        if (i < hi) a[i] = x + before;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += s_w[nw - 1];
+        __syncthreads();
+    }
+}
+
+// Copies one old row's surviving arcs: every lane of the warp calls with the
+// same u; arcs [e0, e1) of the old row. Positions come from the row's cursor,
+// one atomic per warp step.
+__device__ __forceinline__ void copy_piece(int u, long long e0, long long e1, const int *ci,
+                                           const long long *new_rp, int *new_ci, int *cursor,
+                                           unsigned char tflag, const unsigned long long *instab,
+                                           unsigned insmask, const unsigned long long *deltab,
+                                           unsigned delmask, int *err)
+{
+    const unsigned lane = threadIdx.x & 31;
+    for (long long e = e0; e < e1; e += 32) {
+        const long long i = e + lane;
+        int v = -1;
+        bool keep = false;
+        if (i < e1) {
+            v = ci[i];
+            keep = true;
+            if ((tflag & 2) && set_has(deltab, delmask, arc_key(u, v))) keep = false;
+            if ((tflag & 1) && set_has(instab, insmask, arc_key(u, v))) fail(err, kExistingArc);
+        }
+        const unsigned b = __ballot_sync(kFull, keep);
+        int base = 0;
+        if (lane == 0 && b) base = atomicAdd(cursor + u, __popc(b));
+        base = __shfl_sync(kFull, base, 0);
+        if (keep) {
+            const long long pos = new_rp[u] + base + __popc(b & ((1u << lane) - 1u));
+            if (pos < new_rp[u + 1]) new_ci[pos] = v;
+            else fail(err, kMissingArc);
+        }
+    }
+}
+
+constexpr long long kPiece = 4096;   // arcs of a row that one warp copies at a time
+
+// Rows of at most kPiece arcs: one warp per row. Longer rows: every warp
+// takes the pieces (w, w + nwarps, ...) of each of them.
+__global__ void __launch_bounds__(512) copy_kernel(
+    const long long *rp, const int *ci, long long n, const long long *new_rp, int *new_ci,
+    int *cursor, const unsigned char *touched, const int *big, const int *nbig,
+    const unsigned long long *instab, unsigned insmask, const unsigned long long *deltab,
+    unsigned delmask, int *err)
+{
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = gw; u < n; u += nwarps) {
+        const long long e0 = rp[u], e1 = rp[u + 1];
+        if (e1 - e0 <= kPiece)
+            copy_piece((int)u, e0, e1, ci, new_rp, new_ci, cursor, touched[u], instab, insmask,
+                       deltab, delmask, err);
+    }
+    const int nb = *nbig;
+    long long k = gw;   // global piece index over the big rows, in list order
+    for (int j = 0; j < nb; ++j) {
+        const int u = big[j];
+        const long long e0 = rp[u], e1 = rp[u + 1];
+        const long long pieces = (e1 - e0 + kPiece - 1) / kPiece;
+        for (; k < pieces; k += nwarps) {
+            const long long s = e0 + k * kPiece;
+            copy_piece(u, s, s + kPiece < e1 ? s + kPiece : e1, ci, new_rp, new_ci, cursor,
+                       touched[u], instab, insmask, deltab, delmask, err);
+        }
+        k -= pieces;
+    }
+}
+
+// rows longer than kPiece (listed for copy_kernel)
+__global__ void big_rows_kernel(const long long *rp, long long n, int *big, int *nbig)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
+        if (rp[u + 1] - rp[u] > kPiece) big[atomicAdd(nbig, 1)] = (int)u;
+}
+
+// inserted arcs appended after the copies
+__global__ void insert_kernel(const int *ins, long long n_ins, const long long *new_rp,
+                              int *new_ci, int *cursor, int *err)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n_ins;
+         i += stride) {
+        const int u = ins[i], v = ins[i ^ 1];
+        const long long pos = new_rp[u] + atomicAdd(cursor + u, 1);
+        if (pos < new_rp[u + 1]) new_ci[pos] = v;
+        else fail(err, kMissingArc);
+    }
+}
+
+// First active set of the deletion rounds: the deleted edges' endpoints (their
+// neighbourhoods changed, and their estimates may be capped at the new
+// degree) and every neighbour of theirs (whose neighbours' estimates may
+// have fallen). One warp per endpoint; mark[] keeps each vertex once; the
+// list was filled with -1 beforehand.
+__global__ void first_active_kernel(const int *del, long long n_end, const long long *rp,
+                                    const int *ci, int *mark, int *list, int *count)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = gw; i < n_end; i += nwarps) {
+        const int u = del[i];
+        if (lane == 0 && atomicExch(mark + u, 1) == 0) list[atomicAdd(count, 1)] = u;
+        for (long long e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+            const int v = ci[e];
+            if (__ldcg(mark + v) == 0 && atomicExch(mark + v, 1) == 0)
+                list[atomicAdd(count, 1)] = v;
+        }
+    }
+}
+
+// every row filled exactly (a deleted edge that was not in the graph leaves a gap)
+__global__ void check_kernel(const long long *new_rp, long long n, const int *cursor, int *err)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if ((long long)cursor[v] != new_rp[v + 1] - new_rp[v]) fail(err, kMissingArc);
+}
+
+// ---------------------------------------------------------------------------
+// step 3: insertion passes
+// ---------------------------------------------------------------------------
+namespace maint {
+
+enum : int { L_ALLB = 0, L_CS = 1, L_CB = 2, L_QS = 3, L_QB = 4, L_NC = 5, L_RAISED = 6 };
+
+struct Params {
+    const long long *rp;
+    const int *ci;
+    long long n, m;
+    int *core;             // in: a lower bound of the coreness; out: the coreness
+    int *cd;               // neighbours of core >= own (0 at rest)
+    int *sup;              // support of a candidate
+    unsigned char *flag;   // 1 candidate, 3 peeled candidate, 0 otherwise
+    int2 *allb;            // chunks of every large vertex
+    int *cs, *qs;          // candidates, peel queue (small vertices)
+    int2 *cb, *qb;         // their chunks
+    unsigned cap;
+    Ctrl *ctl;
+    Tuning tn;
+    int max_passes;
+};
+
+// support: neighbours of higher core, or of equal core that are candidates
+struct SupArc {
+    static constexpr int kArcs = 4;
+    const int *core;
+    const unsigned char *flag;
+    int *sup;
+    unsigned long long n_arcs = 0;
+    __device__ __forceinline__ bool item(int v, int &a, int &)
+    {
+        a = ldcg(core + v);
+        return true;
+    }
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&vo)[kArcs],
+                                         const int (&u)[kArcs], const long long (&)[kArcs],
+                                         const int (&a)[kArcs], const int (&)[kArcs])
+    {
+        bool s[kArcs];
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            s[j] = false;
+            if (valid[j]) {
+                const int cu = ldcg(core + u[j]);
+                s[j] = cu > a[j] || (cu == a[j] && (__ldcg(flag + u[j]) & 1));
+            }
+        }
+        const bool one = __all_sync(kFull, vo[0] == __shfl_sync(kFull, vo[0], 0) &&
+                                               vo[kArcs - 1] == vo[0]);
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            n_arcs += valid[j];
+            if (one) mine += s[j];
+            else if (s[j]) red_add(sup + vo[j], 1);
+        }
+        if (one) {
+            const int tot = __reduce_add_sync(kFull, mine);
+            if ((threadIdx.x & 31) == 0 && tot) red_add(sup + vo[0], tot);
+        }
+    }
+};
+
+// peel: a peeled candidate w lowers the support of its equal-core candidates
+struct PeelArc {
+    static constexpr int kArcs = 4;
+    const long long *rp;
+    int *core;
+    int *sup;
+    unsigned char *flag;
+    int *qs;
+    int2 *qb;
+    unsigned *c_qs, *c_qb;
+    unsigned n, cap;
+    Ctrl *ctl;
+    Tuning tn;
+    unsigned long long n_arcs = 0, n_atomics = 0;
+    __device__ __forceinline__ bool item(int w, int &a, int &)
+    {
+        a = ldcg(core + w);
+        return true;
+    }
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&)[kArcs],
+                                         const int (&u)[kArcs], const long long (&)[kArcs],
+                                         const int (&a)[kArcs], const int (&)[kArcs])
+    {
+        bool hit[kArcs];
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j)
+            hit[j] = valid[j] && ldcg(core + u[j]) == a[j] && __ldcg(flag + u[j]) == 1;
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            n_arcs += valid[j];
+            bool push = false;
+            if (hit[j]) {
+                ++n_atomics;
+                push = atomicSub(sup + u[j], 1) == a[j] + 1;   // support fell below a + 1
+                if (push) flag[u[j]] = 3;
+            }
+            const long long d = push ? rp[u[j] + 1] - rp[u[j]] : 0;
+            warp_append_vertex(push, u[j], d, qs, c_qs, n, qb, c_qb, cap, ctl, tn);
+        }
+    }
+};
+
+__device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned long long *st,
+                    unsigned long long &arcs, unsigned long long &atomics)
+{
+    Ctrl *ctl = p.ctl;
+    unsigned *live = dom.live();
+    const unsigned *snap = dom.s_snap;
+    const unsigned tid = dom.tid(), nthreads = dom.nthreads();
+    const unsigned gwarp = tid >> 5, nwarps = nthreads >> 5;
+    const long long n = p.n;
+    const long long first = (long long)dom.cta() * blockDim.x;
+
+    for (long long base = first; base < n; base += nthreads) {
+        const long long v = base + threadIdx.x;
+        long long d = 0;
+        if (v < n) {
+            d = p.rp[v + 1] - p.rp[v];
+            p.cd[v] = 0;
+            p.flag[v] = 0;
+        }
+        const unsigned nch =
+            d > p.tn.small_deg ? (unsigned)((d + p.tn.chunk - 1) / p.tn.chunk) : 0u;
+        const unsigned pos = block_alloc(nch, &live[L_ALLB], s_tmp);
+        if (nch && (unsigned long long)pos + nch <= p.cap)
+            for (unsigned c = 0; c < nch; ++c) p.allb[pos + c] = make_int2((int)v, (int)c);
+        else if (nch)
+            set_error(ctl, kErrNotConverged);
+    }
+    if (!dom.sync()) return;
+    if (threadIdx.x == 0) ++st[kStBarriers];
+    const unsigned nallb = snap[L_ALLB];
+
+    for (int pass = 0; pass < p.max_passes; ++pass) {
+        if (dom.leader()) {
+            for (int w = L_CS; w <= L_RAISED; ++w) live[w] = 0;
+        }
+        // A: cd = neighbours of core >= own, for every vertex
+        {
+            i2c::CntArc<long long> f{p.core, p.cd};
+            expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, p.allb, nallb, gwarp, nwarps, f,
+                   p.tn);
+            arcs += f.n_arcs;
+            atomics += f.n_atomics;
+        }
+        if (!dom.sync()) return;
+        if (threadIdx.x == 0) ++st[kStBarriers];
+        // B: candidates
+        for (long long base = first; base < n; base += nthreads) {
+            const long long v = base + threadIdx.x;
+            long long d = 0;
+            bool cand = false;
+            if (v < n) {
+                const int c = ldcg(p.core + v);
+                d = p.rp[v + 1] - p.rp[v];
+                cand = d >= c + 1 && ldcg(p.cd + v) >= c + 1;
+                p.cd[v] = 0;
+                p.sup[v] = 0;
+                p.flag[v] = cand ? 1 : 0;
+            }
+            warp_append_vertex(cand, (int)v, d, p.cs, &live[L_CS], (unsigned)n, p.cb,
+                               &live[L_CB], p.cap, ctl, p.tn);
+            const unsigned c = __popc(__ballot_sync(kFull, cand));
+            if ((threadIdx.x & 31) == 0 && c) atomicAdd(&live[L_NC], c);
+        }
+        if (!dom.sync()) return;
+        if (threadIdx.x == 0) {
+            ++st[kStBarriers];
+            st[kStActive] += snap[L_NC];
+        }
+        if (snap[L_NC] == 0) break;
+        const unsigned ncs = snap[L_CS], ncb = snap[L_CB];
+        // C: support of the candidates
+        {
+            SupArc f{p.core, p.flag, p.sup};
+            expand(p.rp, p.ci, p.cs, ncs, p.cb, ncb, gwarp, nwarps, f, p.tn,
+                   batch_width(ncs, ncb, nwarps));
+            arcs += f.n_arcs;
+        }
+        if (!dom.sync()) return;
+        if (threadIdx.x == 0) ++st[kStBarriers];
+        // D: the candidates without enough support start the peel
+        i2c::for_vertices(
+            p.cs, ncs, p.cb, ncb, tid, nthreads, gwarp, nwarps,
+            [&](bool ok, int v) {
+                bool out = false;
+                long long d = 0;
+                if (ok && ldcg(p.sup + v) < ldcg(p.core + v) + 1) {
+                    out = true;
+                    p.flag[v] = 3;
+                    d = p.rp[v + 1] - p.rp[v];
+                }
+                warp_append_vertex(out, v, d, p.qs, &live[L_QS], (unsigned)n, p.qb, &live[L_QB],
+                                   p.cap, ctl, p.tn);
+            },
+            [&](int v) {
+                if ((threadIdx.x & 31) == 0 && ldcg(p.sup + v) < ldcg(p.core + v) + 1) {
+                    p.flag[v] = 3;
+                    if (!push_chunks(v, p.rp[v + 1] - p.rp[v], p.qb, &live[L_QB], p.cap,
+                                     p.tn.chunk))
+                        set_error(ctl, kErrNotConverged);
+                }
+            });
+        if (!dom.sync()) return;
+        if (threadIdx.x == 0) ++st[kStBarriers];
+        // E: peel wave by wave
+        unsigned s0 = 0, s1 = 0, e0 = snap[L_QS], e1 = snap[L_QB];
+        long long waves = 0;
+        while (s0 < e0 || s1 < e1) {
+            if (++waves > n + 2) {
+                if (threadIdx.x == 0) set_error(ctl, kErrNotConverged);
+                return;
+            }
+            PeelArc f{p.rp,         p.core,       p.sup,       p.flag, p.qs, p.qb,
+                      &live[L_QS],  &live[L_QB],  (unsigned)n, p.cap,  ctl,  p.tn};
+            expand(p.rp, p.ci, p.qs + s0, e0 - s0, p.qb + s1, e1 - s1, gwarp, nwarps, f, p.tn,
+                   batch_width(e0 - s0, e1 - s1, nwarps));
+            arcs += f.n_arcs;
+            atomics += f.n_atomics;
+            if (!dom.sync()) return;
+            if (threadIdx.x == 0) {
+                ++st[kStBarriers];
+                ++st[kStSubrounds];
+            }
+            s0 = e0;
+            s1 = e1;
+            e0 = snap[L_QS];
+            e1 = snap[L_QB];
+        }
+        // F: the survivors rise by one; flags back to 0
+        i2c::for_vertices(
+            p.cs, ncs, p.cb, ncb, tid, nthreads, gwarp, nwarps,
+            [&](bool ok, int v) {
+                bool up = false;
+                if (ok) {
+                    up = __ldcg(p.flag + v) == 1;
+                    if (up) p.core[v] = ldcg(p.core + v) + 1;
+                    p.flag[v] = 0;
+                }
+                const unsigned c = __popc(__ballot_sync(kFull, up));
+                if ((threadIdx.x & 31) == 0 && c) atomicAdd(&live[L_RAISED], c);
+            },
+            [&](int v) {
+                if ((threadIdx.x & 31) == 0) {
+                    if (__ldcg(p.flag + v) == 1) {
+                        p.core[v] = ldcg(p.core + v) + 1;
+                        atomicAdd(&live[L_RAISED], 1u);
+                    }
+                    p.flag[v] = 0;
+                }
+            });
+        if (!dom.sync()) return;
+        if (threadIdx.x == 0) {
+            ++st[kStBarriers];
+            st[kStFrontier] += snap[L_RAISED];
+            if (snap[L_RAISED]) ++st[kStRounds];
+        }
+        if (snap[L_RAISED] == 0) break;
+        if (pass + 1 == p.max_passes && threadIdx.x == 0) set_error(ctl, kErrNotConverged);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    maint_kernel(Params p, LastResult *last, unsigned long long limit_ns)
+{
+    __shared__ unsigned s_snap[kLiveWords + 1];
+    __shared__ unsigned s_tmp[256];
+    __shared__ unsigned long long s_red[32];
+    __shared__ unsigned long long st[kStCount];
+    if (threadIdx.x < kStCount) st[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long arcs = 0, atomics = 0;
+    GridDom dom{p.ctl, s_snap, limit_ns};
+    run(p, dom, s_tmp, st, arcs, atomics);
+    block_sum_to(arcs, &p.ctl->stats[kStArcs], s_red);
+    block_sum_to(atomics, &p.ctl->stats[kStAtomics], s_red);
+    if (blockIdx.x != 0 && threadIdx.x < kStCount) st[threadIdx.x] = 0;
+    finish_block(p.ctl, last, PICO_STATS_MAINTENANCE, st, kStCount);
+}
+
+}  // namespace maint
+
+size_t maint_ws_bytes(long long n, long long m)
+{
+    Carver c(nullptr);
+    c.take<Ctrl>(1);
+    c.take<int>(n);             // cd
+    c.take<int>(n);             // sup
+    c.take<unsigned char>(n);   // flag
+    c.take<int>(n);             // cs
+    c.take<int>(n);             // qs
+    for (int i = 0; i < 3; ++i) c.take<int2>(chunk_capacity(m));
+    return c.size();
+}
+
+}  // namespace dyn
+}  // namespace pico
+
+// ---------------------------------------------------------------------------
+// the state and the C ABI
+// ---------------------------------------------------------------------------
+struct pico_dyn {
+    int device;
+    long long n, m, cap;
+    long long *rp[2];
+    int *ci[2];
+    int cur;
+    int *core;
+};
+
+namespace {
+
+unsigned pow2_at_least(long long x)
+{
+    unsigned p = 1024;
+    while ((long long)p < x && p < (1u << 31)) p <<= 1;
+    return p;
+}
+
+int sync_status(cudaStream_t s)
+{
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    return PICO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                          int64_t capacity_arcs, pico_stream_t stream)
+{
+    if (n < 1 || m < 0 || capacity_arcs < m || !row_ptr || (m > 0 && !col_idx)) return nullptr;
+    if (n >= INT32_MAX || capacity_arcs >= (1ll << 36)) return nullptr;
+    pico::LaunchCfg cfg;
+    pico::LastResult *last = nullptr;
+    if (pico::current_device(&cfg, &last) != PICO_OK) return nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    pico_dyn *d = new pico_dyn();
+    d->device = cfg.device;
+    d->n = n;
+    d->m = m;
+    d->cap = capacity_arcs;
+    d->cur = 0;
+    bool ok = true;
+    for (int i = 0; i < 2 && ok; ++i) {
+        ok = cudaMalloc(&d->rp[i], (size_t)(n + 1) * sizeof(long long)) == cudaSuccess &&
+             cudaMalloc(&d->ci[i], (size_t)(capacity_arcs > 0 ? capacity_arcs : 1) * sizeof(int)) ==
+                 cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&d->core, (size_t)n * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(d->rp[0], row_ptr, (size_t)(n + 1) * sizeof(long long),
+                               cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+    ok = ok && (m == 0 || cudaMemcpyAsync(d->ci[0], col_idx, (size_t)m * sizeof(int),
+                                          cudaMemcpyDeviceToDevice, s) == cudaSuccess);
+    ok = ok && pico_coreness_i64(reinterpret_cast<const int64_t *>(d->rp[0]), d->ci[0], n, m,
+                                 d->core, PICO_ALGO_AUTO, stream) ==
+                   PICO_OK;
+    ok = ok && sync_status(s) == PICO_OK && pico_last_device_status(stream) == PICO_OK;
+    if (!ok) {
+        cudaGetLastError();
+        pico_dyn_destroy(d);
+        return nullptr;
+    }
+    return d;
+}
+
+int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_t *del,
+                    int64_t n_del, pico_stream_t stream)
+{
+    if (!d || n_ins < 0 || n_del < 0 || (n_ins > 0 && !ins) || (n_del > 0 && !del))
+        return PICO_ERR_INVALID_ARG;
+    const long long n = d->n, m_old = d->m, m_new = d->m + 2 * n_ins - 2 * n_del;
+    if (m_new < 0 || m_new > d->cap || n_ins + n_del > (1ll << 28)) return PICO_ERR_INVALID_ARG;
+    if (n_ins == 0 && n_del == 0) return PICO_OK;
+    pico::LaunchCfg cfg;
+    pico::LastResult *last = nullptr;
+    int rc = pico::current_device(&cfg, &last);
+    if (rc != PICO_OK) return rc;
+    if (cfg.device != d->device) return PICO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long *rp = d->rp[d->cur];
+    const int *ci = d->ci[d->cur];
+    long long *nrp = d->rp[1 - d->cur];
+    int *nci = d->ci[1 - d->cur];
+    const unsigned insmask = pow2_at_least(4 * n_ins + 1) - 1, delmask = pow2_at_least(4 * n_del + 1) - 1;
+    // scratch: counts, cursors, flags, big rows, hash sets, scan sums, control block
+    using pico::Carver;
+    Carver c0(nullptr);
+    c0.take<int>(n);                     // ins_cnt
+    c0.take<int>(n);                     // del_cnt
+    c0.take<int>(n);                     // cursor
+    c0.take<unsigned char>(n + 4);       // touched
+    c0.take<int>(n);                     // big rows
+    c0.take<int>(4);                     // nbig, err
+    c0.take<unsigned long long>(insmask + 1ull);
+    c0.take<unsigned long long>(delmask + 1ull);
+    c0.take<long long>(4096);            // scan sums
+    c0.take<pico::Ctrl>(1);
+    c0.take<int>(n);                     // mark (first active set)
+    c0.take<int>(4);                     // its count
+    const size_t zero_bytes = c0.size();
+    c0.take<int>(n);                     // first active set (filled with -1)
+    const size_t pre_bytes = c0.size();
+    const size_t bytes = pre_bytes + std::max(pico::index2core_ws_bytes(n, m_new),
+                                              pico::dyn::maint_ws_bytes(n, m_new));
+    void *ws = nullptr;
+    if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_OOM;
+    }
+    Carver c(ws);
+    int *ins_cnt = c.take<int>(n), *del_cnt = c.take<int>(n), *cursor = c.take<int>(n);
+    unsigned char *touched = c.take<unsigned char>(n + 4);
+    int *big = c.take<int>(n), *flags = c.take<int>(4);
+    unsigned long long *instab = c.take<unsigned long long>(insmask + 1ull);
+    unsigned long long *deltab = c.take<unsigned long long>(delmask + 1ull);
+    long long *sums = c.take<long long>(4096);
+    pico::Ctrl *sctl = c.take<pico::Ctrl>(1);
+    int *amark = c.take<int>(n), *acount = c.take<int>(4);
+    int *alist = c.take<int>(n);
+    void *ws2 = static_cast<char *>(ws) + pre_bytes;
+    int *nbig = flags, *err = flags + 1;
+    const int G = cfg.sms * 4;
+    bool ok = cudaMemsetAsync(ws, 0, zero_bytes, s) == cudaSuccess &&
+              cudaMemsetAsync(static_cast<char *>(ws) + zero_bytes, 0xFF, pre_bytes - zero_bytes,
+                              s) == cudaSuccess;
+    if (ok) {
+        pico::dyn::count_kernel<<<G, 256, 0, s>>>(ins, n_ins, del, n_del, n, ins_cnt, del_cnt,
+                                                 touched, instab, insmask, deltab, delmask, err);
+        pico::dyn::degree_kernel<<<G, 256, 0, s>>>(rp, n, ins_cnt, del_cnt, nrp, err);
+        pico::dyn::big_rows_kernel<<<G, 256, 0, s>>>(rp, n, big, nbig);
+        ok = cudaGetLastError() == cudaSuccess;
+    }
+    if (ok) {   // scan of the new degrees: one CTA per SM, cooperative
+        long long *a = nrp;
+        long long nn = n;
+        unsigned long long limit = cfg.limit_ns;
+        void *args[] = {&a, &nn, &sctl, &sums, &limit};
+        ok = cudaLaunchCooperativeKernel((const void *)pico::dyn::scan_kernel, dim3(cfg.sms),
+                                         dim3(pico::kThreads), args, 0, s) == cudaSuccess;
+    }
+    if (ok) {
+        pico::dyn::copy_kernel<<<cfg.sms * 2, 512, 0, s>>>(rp, ci, n, nrp, nci, cursor, touched,
+                                                           big, nbig, instab, insmask, deltab,
+                                                           delmask, err);
+        if (n_ins > 0)
+            pico::dyn::insert_kernel<<<G, 256, 0, s>>>(ins, n_ins, nrp, nci, cursor, err);
+        pico::dyn::check_kernel<<<G, 256, 0, s>>>(nrp, n, cursor, err);
+        ok = cudaGetLastError() == cudaSuccess;
+    }
+    int herr = 0;
+    ok = ok && sync_status(s) == PICO_OK &&
+         cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    long long m_chk = -1;
+    ok = ok && cudaMemcpy(&m_chk, nrp + n, sizeof(long long), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok || herr != 0 || m_chk != m_new) {
+        cudaGetLastError();
+        cudaFreeAsync(ws, s);
+        return !ok ? PICO_ERR_CUDA : PICO_ERR_BAD_GRAPH;   // the state is unchanged
+    }
+    // the graph is consistent: switch to it and bring the coreness up to date
+    d->cur = 1 - d->cur;
+    d->m = m_new;
+    (void)m_old;
+    if (n_del > 0 && m_new > 0) {
+        pico::dyn::first_active_kernel<<<G, 256, 0, s>>>(del, 2 * n_del, nrp, nci, amark, alist,
+                                                         acount);
+        rc = pico::launch_index2core_from<long long>(nrp, nci, n, m_new, d->core, d->core, alist,
+                                                     (unsigned)n, ws2, last, s, cfg);
+        if (rc != 0 || cudaGetLastError() != cudaSuccess) ok = false;
+    } else if (n_del > 0) {
+        ok = cudaMemsetAsync(d->core, 0, (size_t)n * sizeof(int), s) == cudaSuccess;
+    }
+    if (ok && n_ins > 0) {
+        pico::dyn::maint::Params p{};
+        Carver cw(ws2);
+        p.rp = nrp;
+        p.ci = nci;
+        p.n = n;
+        p.m = m_new;
+        p.core = d->core;
+        p.ctl = cw.take<pico::Ctrl>(1);
+        p.cd = cw.take<int>(n);
+        p.sup = cw.take<int>(n);
+        p.flag = cw.take<unsigned char>(n);
+        p.cs = cw.take<int>(n);
+        p.qs = cw.take<int>(n);
+        p.cap = (unsigned)pico::chunk_capacity(m_new);
+        p.allb = cw.take<int2>(p.cap);
+        p.cb = cw.take<int2>(p.cap);
+        p.qb = cw.take<int2>(p.cap);
+        p.tn = cfg.tn;
+        p.max_passes = (int)std::min<long long>(n_ins + 1, 1ll << 30);
+        ok = cudaMemsetAsync(p.ctl, 0, sizeof(pico::Ctrl), s) == cudaSuccess;
+        if (ok) {
+            static int occ[64] = {};
+            int &o = occ[cfg.device & 63];
+            if (o == 0 &&
+                (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pico::dyn::maint::maint_kernel,
+                                                               pico::kThreads, 0) != cudaSuccess ||
+                 o <= 0))
+                ok = false;
+            if (ok) {
+                const int per_sm = o < cfg.max_blocks_per_sm ? o : cfg.max_blocks_per_sm;
+                unsigned long long limit = cfg.limit_ns;
+                void *args[] = {&p, &last, &limit};
+                ok = cudaLaunchCooperativeKernel((const void *)pico::dyn::maint::maint_kernel,
+                                                 dim3(cfg.sms * per_sm), dim3(pico::kThreads), args,
+                                                 0, s) == cudaSuccess;
+            }
+        }
+    }
+    cudaFreeAsync(ws, s);
+    if (!ok) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    if (sync_status(s) != PICO_OK) return PICO_ERR_CUDA;
+    return pico_last_device_status(stream);
+}
+
+int pico_dyn_coreness(pico_dyn *d, int32_t *out_core, pico_stream_t stream)
+{
+    if (!d || !out_core) return PICO_ERR_INVALID_ARG;
+    if (cudaMemcpyAsync(out_core, d->core, (size_t)d->n * sizeof(int32_t),
+                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    return PICO_OK;
+}
+
+int pico_dyn_graph(pico_dyn *d, const int64_t **row_ptr, const int32_t **col_idx, int64_t *n,
+                   int64_t *m)
+{
+    if (!d || !row_ptr || !col_idx || !n || !m) return PICO_ERR_INVALID_ARG;
+    *row_ptr = reinterpret_cast<const int64_t *>(d->rp[d->cur]);
+    *col_idx = d->ci[d->cur];
+    *n = d->n;
+    *m = d->m;
+    return PICO_OK;
+}
+
+int pico_dyn_copy_graph(pico_dyn *d, int64_t *row_ptr, int32_t *col_idx, pico_stream_t stream)
+{
+    if (!d || !row_ptr || (d->m > 0 && !col_idx)) return PICO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(row_ptr, d->rp[d->cur], (size_t)(d->n + 1) * sizeof(int64_t),
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        (d->m > 0 && cudaMemcpyAsync(col_idx, d->ci[d->cur], (size_t)d->m * sizeof(int32_t),
+                                     cudaMemcpyDeviceToDevice, s) != cudaSuccess)) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    return PICO_OK;
+}
+
+void pico_dyn_destroy(pico_dyn *d)
+{
+    if (!d) return;
+    for (int i = 0; i < 2; ++i) {
+        if (d->rp[i]) cudaFree(d->rp[i]);
+        if (d->ci[i]) cudaFree(d->ci[i]);
+    }
+    if (d->core) cudaFree(d->core);
+    cudaGetLastError();
+    delete d;
+}
+
+}  // extern "C"

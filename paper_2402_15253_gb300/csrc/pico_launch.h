@@ -68,6 +68,11 @@ int launch_index2core(const Off *rp, const int *ci, long long n, long long m, in
                       void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg,
                       bool use_cnt);
 
+// core maintenance (dyn.cu)
+namespace dyn {
+size_t maint_ws_bytes(long long n, long long m);
+}
+
 // method selection per graph (hybrid.cu)
 size_t hybrid_ws_bytes(long long n, long long m);
 
@@ -82,5 +87,16 @@ int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const 
                    int algo, void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
 
 int selftest_wait_timeout(LastResult *last, int limit_ms, cudaStream_t stream, const LaunchCfg &cfg);
+
+// The current device's launch configuration and per-device status record
+// (capi.cu); returns a pico_status.
+int current_device(LaunchCfg *cfg, LastResult **last);
+
+// Index2core (NbrCore) rounds from given estimates and a first active set
+// (core maintenance, dyn.cu); core may alias init_est.
+template <typename Off>
+int launch_index2core_from(const Off *rp, const int *ci, long long n, long long m, int *core,
+                           const int *init_est, const int *init_active, unsigned n_init,
+                           void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
 
 }  // namespace pico

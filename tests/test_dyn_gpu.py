@@ -1,0 +1,144 @@
+"""GPU tests of core maintenance (pico_dyn_*): after every batch of edge
+insertions and deletions, the maintained coreness must equal the oracle's
+(Batagelj-Zaversnik) on the updated graph, and the maintained CSR must hold
+exactly the updated edge set."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pico():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_15253_gb300 as p
+    torch.cuda.set_device(0)
+    return p
+
+
+def edges_of(g):
+    rp, ci = g.numpy()
+    src = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return {(int(a), int(b)) for a, b in zip(src, ci) if a < b}
+
+
+def check(pico, dg, n, edges):
+    g = gg.from_edge_list(sorted(edges), n)
+    rp, ci = g.numpy()
+    want = oracle.bz_coreness(rp, ci)
+    got = dg.coreness().cpu().numpy()
+    assert np.array_equal(got, want)
+    drp, dci = dg.csr()
+    drp, dci = drp.cpu().numpy(), dci.cpu().numpy()
+    assert drp[-1] == 2 * len(edges)
+    src = np.repeat(np.arange(n), np.diff(drp))
+    got_arcs = set(zip(src.tolist(), dci.tolist()))
+    want_arcs = {(a, b) for a, b in edges} | {(b, a) for a, b in edges}
+    assert got_arcs == want_arcs
+
+
+def random_batch(rng, n, edges, k_ins, k_del):
+    cur = sorted(edges)
+    dele = [cur[i] for i in rng.choice(len(cur), size=min(k_del, len(cur)), replace=False)] \
+        if cur and k_del else []
+    ins = set()
+    while len(ins) < k_ins:
+        a, b = (int(x) for x in rng.integers(0, n, size=2))
+        if a == b:
+            continue
+        e = (min(a, b), max(a, b))
+        if e not in edges and e not in ins:
+            ins.add(e)
+    return sorted(ins), dele
+
+
+def test_closed_forms(pico):
+    # a path becomes a cycle (core 1 -> 2); four vertices on a path become K4
+    # in one batch (a rise by two, several passes)
+    dg = pico.DynamicGraph(gg.path_graph(6).row_ptr.cuda(), gg.path_graph(6).col_idx.cuda())
+    dg.update(insert=[(0, 5)])
+    assert (dg.coreness().cpu() == 2).all()
+    p4 = gg.path_graph(4)
+    dg = pico.DynamicGraph(p4.row_ptr.cuda(), p4.col_idx.cuda())
+    dg.update(insert=[(0, 2), (1, 3), (0, 3)])
+    assert dg.coreness().cpu().tolist() == [3, 3, 3, 3]
+    st = pico.pico_get_stats()
+    assert st["algo"] == pico.PICO_STATS_MAINTENANCE and st["rounds"] >= 2
+    # K6 minus one edge: 5, 5, 4... then every edge removed
+    k6 = gg.complete_graph(6)
+    dg = pico.DynamicGraph(k6.row_ptr.cuda(), k6.col_idx.cuda())
+    dg.update(delete=[(0, 1)])
+    assert dg.coreness().cpu().tolist() == [4] * 6
+    dg.update(delete=sorted(edges_of(k6) - {(0, 1)}))
+    assert (dg.coreness().cpu() == 0).all()
+
+
+def test_isolated_vertices_join_in_a_mixed_batch(pico):
+    # vertices 6..9 start isolated (estimate 0) and gain edges in the same
+    # batch that deletes others: the deletion rounds see estimates of 0
+    edges = {(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 5), (5, 3)}
+    g = gg.from_edge_list(sorted(edges), 10)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=200)
+    ins = [(6, 0), (6, 1), (7, 6), (7, 0), (8, 9), (9, 3)]
+    dele = [(2, 3), (4, 5)]
+    dg.update(insert=ins, delete=dele)
+    check(pico, dg, 10, (edges - set(dele)) | set(ins))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_small_graphs(pico, seed):
+    rng = np.random.default_rng(seed)
+    for trial in range(6):
+        n = int(rng.integers(5, 60))
+        p = [0.05, 0.15, 0.3][trial % 3]
+        edges = {(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p}
+        g = gg.from_edge_list(sorted(edges), n)
+        dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=n * n)
+        for _ in range(4):
+            ins, dele = random_batch(rng, n, edges, int(rng.integers(0, 8)), int(rng.integers(0, 8)))
+            dg.update(insert=ins, delete=dele)
+            edges = (edges - set(dele)) | set(ins)
+            check(pico, dg, n, edges)
+
+
+@pytest.mark.parametrize("name,make", [("rmat15", lambda: gg.rmat_graph(15, 16, 71)),
+                                       ("er-20k", lambda: gg.er_graph(20000, 120000, 72)),
+                                       ("grid-120", lambda: gg.grid_graph(120, 120))])
+def test_batches_on_larger_graphs(pico, name, make):
+    rng = np.random.default_rng(73)
+    g = make()
+    n = g.n
+    edges = edges_of(g)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=2 * g.arcs)
+    for k_ins, k_del in [(500, 0), (0, 500), (2000, 2000), (50, 3000)]:
+        ins, dele = random_batch(rng, n, edges, k_ins, k_del)
+        dg.update(insert=ins, delete=dele)
+        edges = (edges - set(dele)) | set(ins)
+        check(pico, dg, n, edges)
+
+
+def test_bad_batches_leave_the_state_unchanged(pico):
+    g = gg.cycle_graph(10)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=100)
+    bad = [dict(delete=[(0, 5)]),            # not an edge
+           dict(insert=[(0, 1)]),            # already an edge
+           dict(insert=[(2, 2)]),            # self-loop
+           dict(insert=[(0, 10)]),           # vertex out of range
+           dict(insert=[(0, 4), (4, 0)]),    # the same edge twice
+           dict(delete=[(0, 1), (1, 0)])]
+    for b in bad:
+        with pytest.raises(pico.PicoError) as e:
+            dg.update(**b)
+        assert e.value.status == pico.PICO_ERR_BAD_GRAPH, b
+        check(pico, dg, 10, edges_of(g))
+    small = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=24)
+    with pytest.raises(pico.PicoError) as e:   # 26 arcs > capacity 24
+        small.update(insert=[(0, 2), (0, 4), (0, 6)])
+    assert e.value.status == pico.PICO_ERR_INVALID_ARG
+    small.update(insert=[(0, 2), (0, 4)])     # 24 arcs fit
+    check(pico, small, 10, edges_of(g) | {(0, 2), (0, 4)})
