@@ -471,6 +471,80 @@ def bench_auto(pico, rp, ci, n, arcs, ref, stream, reps=3):
             "method": {v: k for k, v in pico.ALGOS.items()}[chose]}
 
 
+def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6):
+    """Core maintenance on the workload graph: batches of k random edge
+    insertions (non-edges), k random deletions (existing edges) and both,
+    each timed with CUDA events around pico_dyn_update, against a full
+    recomputation (PICO_ALGO_AUTO) of the updated graph. The maintained
+    coreness must equal the recomputed one."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    n = g.n
+    rp_h = g.row_ptr.to(torch.int64).cpu().numpy()
+    ci_h = g.col_idx.cpu().numpy()
+    deg = np.diff(rp_h)
+    idx = np.arange(4 * k, dtype=np.int64)
+    # random non-edges (rows are sorted: a binary search rules out existing edges)
+    cu = gg.draw_below(seed, 1, torch.from_numpy(idx), n).numpy()
+    cv = gg.draw_below(seed, 2, torch.from_numpy(idx), n).numpy()
+    ins, seen = [], set()
+    for a, b in zip(cu.tolist(), cv.tolist()):
+        if a == b:
+            continue
+        e = (min(a, b), max(a, b))
+        row = ci_h[rp_h[e[0]]:rp_h[e[0] + 1]]
+        j = np.searchsorted(row, e[1])
+        if e in seen or (j < len(row) and row[j] == e[1]):
+            continue
+        seen.add(e)
+        ins.append(e)
+        if len(ins) == 2 * k:
+            break
+    # random existing edges (arcs drawn uniformly, each edge once)
+    arcs = gg.draw_below(seed, 3, torch.from_numpy(idx), int(rp_h[-1])).numpy()
+    src = np.searchsorted(rp_h, arcs, side="right") - 1
+    dele, dseen = [], set()
+    for a, b in zip(src.tolist(), ci_h[arcs].tolist()):
+        e = (min(a, b), max(a, b))
+        if e not in dseen:
+            dseen.add(e)
+            dele.append(e)
+        if len(dele) == 2 * k:
+            break
+    dev = g.row_ptr.device
+    dg = pico.DynamicGraph(g.row_ptr, g.col_idx, capacity_arcs=g.arcs + 4 * k + 1024)
+    batches = {"insert": (ins[:k], []), "delete": ([], dele[:k]),
+               "mixed": (ins[k:2 * k], dele[k:2 * k])}
+    res = {"batch_edges": k, "graph": "the workload graph", "runs": {}}
+    for name, (bi, bd) in batches.items():
+        ti = torch.tensor(bi, dtype=torch.int32, device=dev).reshape(-1, 2) if bi else None
+        td = torch.tensor(bd, dtype=torch.int32, device=dev).reshape(-1, 2) if bd else None
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = pico.pico_dyn_update(dg._d, ti, len(bi), td, len(bd), stream)
+        e1.record(stream)
+        e1.synchronize()
+        if rc != pico.PICO_OK:
+            raise pico.PicoError(rc, "pico_dyn_update")
+        st = pico.pico_get_stats(stream)
+        rp2, ci2 = dg.csr()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        full = pico.coreness(rp2, ci2, "auto")
+        r1.record(stream)
+        r1.synchronize()
+        if not torch.equal(full, dg.coreness()):
+            raise AssertionError(f"maintained coreness differs after the {name} batch")
+        res["runs"][name] = {"update_ms": e0.elapsed_time(e1),
+                             "recompute_ms": r0.elapsed_time(r1),
+                             "speedup": r0.elapsed_time(r1) / e0.elapsed_time(e1),
+                             "stats": {x: st[x] for x in ("algo", "rounds", "frontier", "active")}}
+    dg.close()
+    return res
+
+
 def job_totals(local_ms: float, local_units: int, device=None):
     """Whole-job time and work over the ranks of the current process group
     (or this process alone): the slowest rank's time and the sum of the
@@ -541,6 +615,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-maintenance", action="store_true",
+                    help="skip the core-maintenance batches")
     ap.add_argument("--no-baselines", action="store_true",
                     help="skip the comparison baselines of the paper's evaluation")
     ap.add_argument("--batch-graphs", type=int, default=4096)
@@ -731,6 +807,8 @@ def main():
         line["baselines"] = bench_baselines(pico, rp, ci, n, arcs, out["peelone"], tuned,
                                             {a: statistics.median(v) for a, v in per.items()},
                                             stream)
+    if rank == 0 and not args.no_maintenance:
+        line["maintenance"] = bench_maintenance(pico, g, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)
     if rank == 0 and args.serve_requests > 0:

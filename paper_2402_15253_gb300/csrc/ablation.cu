@@ -154,54 +154,6 @@ int launch_index2core(const Off *rp, const int *ci, long long n, long long m, in
     return 0;
 }
 
-template <typename Off>
-int launch_index2core_from(const Off *rp, const int *ci, long long n, long long m, int *core,
-                           const int *init_est, const int *init_active, unsigned n_init,
-                           void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg)
-{
-    Carver c(ws);
-    i2c::Params<Off> p;
-    p.rp = rp;
-    p.ci = ci;
-    p.n = n;
-    p.m = m;
-    p.core = core;
-    p.ctl = c.take<Ctrl>(1);
-    p.est = c.take<int>(n);
-    p.newv = c.take<int>(n);
-    p.cnt = c.take<int>(n);
-    p.stamp = c.take<int>(n);
-    p.hist = c.take<int>(m);
-    p.as[0] = c.take<int>(n);
-    p.as[1] = c.take<int>(n);
-    p.fs = c.take<int>(n);
-    p.cs = c.take<int>(n);
-    p.cap = (unsigned)chunk_capacity(m);
-    p.ab[0] = c.take<int2>(p.cap);
-    p.ab[1] = c.take<int2>(p.cap);
-    p.fb = c.take<int2>(p.cap);
-    p.cb = c.take<int2>(p.cap);
-    p.tn = cfg.tn;
-    p.init_est = init_est;
-    p.init_active = init_active;
-    p.n_init = n_init;
-    if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
-    static int occ[64] = {};
-    const void *fn = (const void *)i2c_kernel<Off, false>;
-    const int grid = persistent_grid(fn, cfg, occ);
-    if (grid <= 0) return -3;
-    unsigned long long limit = cfg.limit_ns;
-    void *args[] = {&p, &last, &limit};
-    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, stream) !=
-        cudaSuccess)
-        return -3;
-    return 0;
-}
-
-template int launch_index2core_from<long long>(const long long *, const int *, long long,
-                                               long long, int *, const int *, const int *,
-                                               unsigned, void *, LastResult *, cudaStream_t,
-                                               const LaunchCfg &);
 template int launch_gpp<int>(const int *, const int *, long long, long long, int *, void *,
                              LastResult *, cudaStream_t, const LaunchCfg &);
 template int launch_gpp<long long>(const long long *, const int *, long long, long long, int *,

@@ -194,13 +194,6 @@ struct Params {
     unsigned cap;              // entries of each chunk list
     Ctrl *ctl;
     Tuning tn;
-    // Start (core maintenance): estimates min(init_est[v], deg v) instead of the
-    // degrees, and the first active set init_active[0..n_init) (duplicates
-    // allowed, negative entries skipped) instead of every non-isolated vertex;
-    // nullptr: the defaults.
-    const int *init_est = nullptr;
-    const int *init_active = nullptr;
-    unsigned n_init = 0;
 };
 
 // CntCore: cnt[v] += |{arcs (v, u) : est[u] >= est[v]}|
@@ -269,8 +262,7 @@ struct HistArc {
 #pragma unroll
         for (int j = 0; j < kArcs; ++j) {
             n_arcs += valid[j];
-            // slot min(e, K); a 0 (an estimate of 0 on either side, possible
-            // when maintenance starts from given estimates) supports no h >= 1
+            // slot min(e, K); a 0 would support no h >= 1
             const int s = e[j] < K[j] ? e[j] : K[j];
             if (valid[j] && s > 0) {
                 ++n_atomics;
@@ -381,49 +373,24 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
     const long long n = p.n;
     const long long first = (long long)dom.cta() * blockDim.x;
 
-    // estimates = degrees (or the given start); the first active set is every
-    // non-isolated vertex (or the given list)
+    // estimates = degrees; the first active set is every non-isolated vertex
     for (long long base = first; base < n; base += nthreads) {
         const long long v = base + threadIdx.x;
         long long d = 0;
         if (v < n) {
             d = (long long)(p.rp[v + 1] - p.rp[v]);
-            const int e0 = p.init_est ? ldcg(p.init_est + v) : (int)d;
-            p.est[v] = e0 < (int)d ? e0 : (int)d;
+            p.est[v] = (int)d;
             p.stamp[v] = 0;
             if (UseCnt) p.cnt[v] = 0;
         }
-        const bool act = !p.init_active && d > 0;
-        warp_append_vertex(act, (int)v, d, p.as[0], &live[L_AS], (unsigned)n, p.ab[0],
+        warp_append_vertex(d > 0, (int)v, d, p.as[0], &live[L_AS], (unsigned)n, p.ab[0],
                            &live[L_AB], p.cap, ctl, p.tn);
-        const unsigned c = __popc(__ballot_sync(kFull, act));
+        const unsigned c = __popc(__ballot_sync(kFull, d > 0));
         if ((threadIdx.x & 31) == 0 && c) atomicAdd(&live[L_NACT], c);
     }
     for (long long i = first + threadIdx.x; i < p.m; i += nthreads) p.hist[i] = 0;
     if (!dom.sync()) return;
     if (threadIdx.x == 0) ++st[kStBarriers];
-    if (p.init_active) {   // the given vertices, once each (stamp -1 marks them)
-        for (long long base = first; base < (long long)p.n_init; base += nthreads) {
-            const long long i = base + threadIdx.x;
-            int v = 0;
-            long long d = 0;
-            bool fresh = false;
-            if (i < (long long)p.n_init) {
-                v = ldcg(p.init_active + i);   // entries < 0 are skipped
-                if (v >= 0) {
-                    d = (long long)(p.rp[v + 1] - p.rp[v]);
-                    fresh = d > 0 && atomicExch(p.stamp + v, -1) != -1;
-                }
-            }
-            warp_append_vertex(fresh, v, d, p.as[0], &live[L_AS], (unsigned)n, p.ab[0],
-                               &live[L_AB], p.cap, ctl, p.tn);
-            const unsigned c = __popc(__ballot_sync(kFull, fresh));
-            if ((threadIdx.x & 31) == 0 && c) atomicAdd(&live[L_NACT], c);
-        }
-        if (!dom.sync()) return;
-        if (threadIdx.x == 0) ++st[kStBarriers];
-    }
-
     const long long max_rounds = p.m + 2;
     for (long long r = 0;; ++r) {
         const int par = (int)(r & 1), np = 1 - par;

@@ -8,11 +8,13 @@
 //      the surviving arcs copied row by row (a deleted arc is found in a hash
 //      set of the batch's deleted arcs), the inserted arcs appended.
 //   2. Deletions: coreness can only fall. The old coreness (capped at the new
-//      degree) is an upper bound, so the synchronous h-index iteration of
-//      Alg. 2, started from it with the deleted edges' endpoints as the first
-//      active set (the NbrCore rounds of ablation.cuh), converges to the new
-//      coreness: every fixpoint of HINDEX lies below the coreness, and the
-//      iteration never goes below it.
+//      degree, at least 1) is an upper bound, so HistoCore's rounds (Alg. 6)
+//      started from it instead of the degrees end at the new coreness: they
+//      stop with cnt >= estimate everywhere, which bounds the estimates by the
+//      coreness, and never go below it. Only the vertices whose cnt fell
+//      below their estimate, and those their changes reach, do any work.
+//      With insertions in the batch the start is not an upper bound, but the
+//      result is still a lower bound of the new coreness.
 //   3. Insertions: coreness can only rise; the value after step 2 is a lower
 //      bound. A pass tries to raise every vertex by one: the candidates are
 //      the vertices w with at least core(w) + 1 neighbours of core >= core(w);
@@ -224,21 +226,87 @@ __device__ __forceinline__ void copy_piece(int u, long long e0, long long e1, co
 
 constexpr long long kPiece = 4096;   // arcs of a row that one warp copies at a time
 
-// Rows of at most kPiece arcs: one warp per row. Longer rows: every warp
-// takes the pieces (w, w + nwarps, ...) of each of them.
-__global__ void __launch_bounds__(512) copy_kernel(
-    const long long *rp, const int *ci, long long n, const long long *new_rp, int *new_ci,
-    int *cursor, const unsigned char *touched, const int *big, const int *nbig,
+// tp[v + 1] = 1 for a row the batch touches (scanned afterwards: then tp[v + 1]
+// counts the touched rows up to v)
+__global__ void flag_kernel(const unsigned char *touched, long long n, long long *tp)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        tp[v + 1] = touched[v] ? 1 : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) tp[0] = 0;
+}
+
+// The touched rows in increasing order (T), their old arc ranges and the
+// shift of the untouched rows that follow each of them; the touched rows
+// longer than kPiece are also listed in big.
+__global__ void segments_kernel(const unsigned char *touched, long long n, const long long *tp,
+                                const long long *rp, const long long *new_rp, int *T,
+                                long long *seg_start, long long *seg_end, long long *shift,
+                                int *big, int *nbig)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (!touched[v]) continue;
+        const long long i = tp[v + 1] - 1;
+        T[i] = (int)v;
+        seg_start[i] = rp[v];
+        seg_end[i] = rp[v + 1];
+        shift[i] = new_rp[v + 1] - rp[v + 1];
+        if (rp[v + 1] - rp[v] > kPiece) big[atomicAdd(nbig, 1)] = (int)v;
+    }
+}
+
+// The arcs of the untouched rows keep their order and move by the shift of
+// the touched row before them (0 before the first): one coalesced pass over
+// the old arcs, 1024 per warp, with a binary search once per warp.
+__global__ void __launch_bounds__(512) bulk_copy_kernel(const int *ci, long long m_old,
+                                                        int *new_ci, const long long *seg_start,
+                                                        const long long *seg_end,
+                                                        const long long *shift, const long long *ntp)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const long long nT = *ntp;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c0 = gw * 1024; c0 < m_old; c0 += nwarps * 1024) {
+        long long i = -1;   // last touched row starting at or before c0
+        if (lane == 0) {
+            long long lo = 0, hi = nT;   // first index with seg_start > c0
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (seg_start[mid] <= c0) lo = mid + 1;
+                else hi = mid;
+            }
+            i = lo - 1;
+        }
+        i = __shfl_sync(kFull, i, 0);
+        const long long c1 = c0 + 1024 < m_old ? c0 + 1024 : m_old;
+        for (long long e = c0 + lane; e < c1; e += 32) {
+            while (i + 1 < nT && seg_start[i + 1] <= e) ++i;
+            if (i >= 0 && e < seg_end[i]) continue;   // a touched row: copied elsewhere
+            new_ci[e + (i >= 0 ? shift[i] : 0)] = ci[e];
+        }
+    }
+}
+
+// Touched rows: the surviving arcs, checked against the batch's arc sets.
+// Rows of at most kPiece arcs one warp each; longer ones (big) piece by
+// piece, every warp taking pieces (w, w + nwarps, ...).
+__global__ void __launch_bounds__(512) touched_copy_kernel(
+    const long long *rp, const int *ci, const int *T, const long long *ntp, const long long *new_rp,
+    int *new_ci, int *cursor, const unsigned char *touched, const int *big, const int *nbig,
     const unsigned long long *instab, unsigned insmask, const unsigned long long *deltab,
     unsigned delmask, int *err)
 {
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long u = gw; u < n; u += nwarps) {
+    const long long nT = *ntp;
+    for (long long j = gw; j < nT; j += nwarps) {
+        const int u = T[j];
         const long long e0 = rp[u], e1 = rp[u + 1];
         if (e1 - e0 <= kPiece)
-            copy_piece((int)u, e0, e1, ci, new_rp, new_ci, cursor, touched[u], instab, insmask,
-                       deltab, delmask, err);
+            copy_piece(u, e0, e1, ci, new_rp, new_ci, cursor, touched[u], instab, insmask, deltab,
+                       delmask, err);
     }
     const int nb = *nbig;
     long long k = gw;   // global piece index over the big rows, in list order
@@ -255,14 +323,6 @@ __global__ void __launch_bounds__(512) copy_kernel(
     }
 }
 
-// rows longer than kPiece (listed for copy_kernel)
-__global__ void big_rows_kernel(const long long *rp, long long n, int *big, int *nbig)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
-        if (rp[u + 1] - rp[u] > kPiece) big[atomicAdd(nbig, 1)] = (int)u;
-}
-
 // inserted arcs appended after the copies
 __global__ void insert_kernel(const int *ins, long long n_ins, const long long *new_rp,
                               int *new_ci, int *cursor, int *err)
@@ -277,34 +337,17 @@ __global__ void insert_kernel(const int *ins, long long n_ins, const long long *
     }
 }
 
-// First active set of the deletion rounds: the deleted edges' endpoints (their
-// neighbourhoods changed, and their estimates may be capped at the new
-// degree) and every neighbour of theirs (whose neighbours' estimates may
-// have fallen). One warp per endpoint; mark[] keeps each vertex once; the
-// list was filled with -1 beforehand.
-__global__ void first_active_kernel(const int *del, long long n_end, const long long *rp,
-                                    const int *ci, int *mark, int *list, int *count)
+// every touched row filled exactly (a deleted edge that was not in the graph
+// leaves a gap; untouched rows are copied whole)
+__global__ void check_kernel(const int *T, const long long *ntp, const long long *new_rp,
+                             const int *cursor, int *err)
 {
-    const unsigned lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long i = gw; i < n_end; i += nwarps) {
-        const int u = del[i];
-        if (lane == 0 && atomicExch(mark + u, 1) == 0) list[atomicAdd(count, 1)] = u;
-        for (long long e = rp[u] + lane; e < rp[u + 1]; e += 32) {
-            const int v = ci[e];
-            if (__ldcg(mark + v) == 0 && atomicExch(mark + v, 1) == 0)
-                list[atomicAdd(count, 1)] = v;
-        }
-    }
-}
-
-// every row filled exactly (a deleted edge that was not in the graph leaves a gap)
-__global__ void check_kernel(const long long *new_rp, long long n, const int *cursor, int *err)
-{
+    const long long nT = *ntp;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nT; j += stride) {
+        const int v = T[j];
         if ((long long)cursor[v] != new_rp[v + 1] - new_rp[v]) fail(err, kMissingArc);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -701,25 +744,27 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     long long *nrp = d->rp[1 - d->cur];
     int *nci = d->ci[1 - d->cur];
     const unsigned insmask = pow2_at_least(4 * n_ins + 1) - 1, delmask = pow2_at_least(4 * n_del + 1) - 1;
-    // scratch: counts, cursors, flags, big rows, hash sets, scan sums, control block
+    // scratch: counts, cursors, flags, touched-row lists, hash sets, scans
+    const long long nt_cap = std::min<long long>(n, 2 * (n_ins + n_del));
     using pico::Carver;
     Carver c0(nullptr);
     c0.take<int>(n);                     // ins_cnt
     c0.take<int>(n);                     // del_cnt
     c0.take<int>(n);                     // cursor
     c0.take<unsigned char>(n + 4);       // touched
-    c0.take<int>(n);                     // big rows
     c0.take<int>(4);                     // nbig, err
     c0.take<unsigned long long>(insmask + 1ull);
     c0.take<unsigned long long>(delmask + 1ull);
     c0.take<long long>(4096);            // scan sums
     c0.take<pico::Ctrl>(1);
-    c0.take<int>(n);                     // mark (first active set)
-    c0.take<int>(4);                     // its count
+    c0.take<pico::Ctrl>(1);
     const size_t zero_bytes = c0.size();
-    c0.take<int>(n);                     // first active set (filled with -1)
+    c0.take<long long>(n + 1);           // touched-row scan
+    c0.take<int>(nt_cap);                // touched rows in order
+    c0.take<int>(nt_cap);                // the long ones
+    for (int i = 0; i < 3; ++i) c0.take<long long>(nt_cap);   // their arc ranges, shifts
     const size_t pre_bytes = c0.size();
-    const size_t bytes = pre_bytes + std::max(pico::index2core_ws_bytes(n, m_new),
+    const size_t bytes = pre_bytes + std::max(pico::histocore_ws_bytes(n, m_new),
                                               pico::dyn::maint_ws_bytes(n, m_new));
     void *ws = nullptr;
     if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
@@ -729,41 +774,45 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     Carver c(ws);
     int *ins_cnt = c.take<int>(n), *del_cnt = c.take<int>(n), *cursor = c.take<int>(n);
     unsigned char *touched = c.take<unsigned char>(n + 4);
-    int *big = c.take<int>(n), *flags = c.take<int>(4);
+    int *flags = c.take<int>(4);
     unsigned long long *instab = c.take<unsigned long long>(insmask + 1ull);
     unsigned long long *deltab = c.take<unsigned long long>(delmask + 1ull);
     long long *sums = c.take<long long>(4096);
-    pico::Ctrl *sctl = c.take<pico::Ctrl>(1);
-    int *amark = c.take<int>(n), *acount = c.take<int>(4);
-    int *alist = c.take<int>(n);
+    pico::Ctrl *sctl = c.take<pico::Ctrl>(1), *sctl2 = c.take<pico::Ctrl>(1);
+    long long *tp = c.take<long long>(n + 1);
+    int *T = c.take<int>(nt_cap), *big = c.take<int>(nt_cap);
+    long long *seg_start = c.take<long long>(nt_cap), *seg_end = c.take<long long>(nt_cap);
+    long long *shift = c.take<long long>(nt_cap);
     void *ws2 = static_cast<char *>(ws) + pre_bytes;
     int *nbig = flags, *err = flags + 1;
     const int G = cfg.sms * 4;
-    bool ok = cudaMemsetAsync(ws, 0, zero_bytes, s) == cudaSuccess &&
-              cudaMemsetAsync(static_cast<char *>(ws) + zero_bytes, 0xFF, pre_bytes - zero_bytes,
-                              s) == cudaSuccess;
+    auto scan = [&](long long *arr, pico::Ctrl *ctl) {   // in-place scan of arr[1..n]
+        long long *a = arr;
+        long long nn = n;
+        unsigned long long limit = cfg.limit_ns;
+        void *args[] = {&a, &nn, &ctl, &sums, &limit};
+        return cudaLaunchCooperativeKernel((const void *)pico::dyn::scan_kernel, dim3(cfg.sms),
+                                           dim3(pico::kThreads), args, 0, s) == cudaSuccess;
+    };
+    bool ok = cudaMemsetAsync(ws, 0, zero_bytes, s) == cudaSuccess;
     if (ok) {
         pico::dyn::count_kernel<<<G, 256, 0, s>>>(ins, n_ins, del, n_del, n, ins_cnt, del_cnt,
                                                  touched, instab, insmask, deltab, delmask, err);
         pico::dyn::degree_kernel<<<G, 256, 0, s>>>(rp, n, ins_cnt, del_cnt, nrp, err);
-        pico::dyn::big_rows_kernel<<<G, 256, 0, s>>>(rp, n, big, nbig);
-        ok = cudaGetLastError() == cudaSuccess;
-    }
-    if (ok) {   // scan of the new degrees: one CTA per SM, cooperative
-        long long *a = nrp;
-        long long nn = n;
-        unsigned long long limit = cfg.limit_ns;
-        void *args[] = {&a, &nn, &sctl, &sums, &limit};
-        ok = cudaLaunchCooperativeKernel((const void *)pico::dyn::scan_kernel, dim3(cfg.sms),
-                                         dim3(pico::kThreads), args, 0, s) == cudaSuccess;
+        pico::dyn::flag_kernel<<<G, 256, 0, s>>>(touched, n, tp);
+        ok = cudaGetLastError() == cudaSuccess && scan(nrp, sctl) && scan(tp, sctl2);
     }
     if (ok) {
-        pico::dyn::copy_kernel<<<cfg.sms * 2, 512, 0, s>>>(rp, ci, n, nrp, nci, cursor, touched,
-                                                           big, nbig, instab, insmask, deltab,
-                                                           delmask, err);
+        pico::dyn::segments_kernel<<<G, 256, 0, s>>>(touched, n, tp, rp, nrp, T, seg_start,
+                                                    seg_end, shift, big, nbig);
+        pico::dyn::bulk_copy_kernel<<<cfg.sms * 2, 512, 0, s>>>(ci, m_old, nci, seg_start, seg_end,
+                                                               shift, tp + n);
+        pico::dyn::touched_copy_kernel<<<cfg.sms * 2, 512, 0, s>>>(
+            rp, ci, T, tp + n, nrp, nci, cursor, touched, big, nbig, instab, insmask, deltab,
+            delmask, err);
         if (n_ins > 0)
             pico::dyn::insert_kernel<<<G, 256, 0, s>>>(ins, n_ins, nrp, nci, cursor, err);
-        pico::dyn::check_kernel<<<G, 256, 0, s>>>(nrp, n, cursor, err);
+        pico::dyn::check_kernel<<<G, 256, 0, s>>>(T, tp + n, nrp, cursor, err);
         ok = cudaGetLastError() == cudaSuccess;
     }
     int herr = 0;
@@ -779,12 +828,9 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     // the graph is consistent: switch to it and bring the coreness up to date
     d->cur = 1 - d->cur;
     d->m = m_new;
-    (void)m_old;
     if (n_del > 0 && m_new > 0) {
-        pico::dyn::first_active_kernel<<<G, 256, 0, s>>>(del, 2 * n_del, nrp, nci, amark, alist,
-                                                         acount);
-        rc = pico::launch_index2core_from<long long>(nrp, nci, n, m_new, d->core, d->core, alist,
-                                                     (unsigned)n, ws2, last, s, cfg);
+        rc = pico::launch_histocore<long long>(nrp, nci, n, m_new, d->core, ws2, last, s, cfg,
+                                               d->core);
         if (rc != 0 || cudaGetLastError() != cudaSuccess) ok = false;
     } else if (n_del > 0) {
         ok = cudaMemsetAsync(d->core, 0, (size_t)n * sizeof(int), s) == cudaSuccess;

@@ -53,7 +53,8 @@ size_t histocore_ws_bytes(long long n, long long m)
 
 template <typename Off>
 int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int *core,
-                     void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg)
+                     void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg,
+                     const int *init_est)
 {
     Carver c(ws);
     histo::Params<Off> p;
@@ -78,6 +79,7 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
     p.ib = c.take<int2>(p.ub_cap);
     p.zero_histo = false;
     p.tn = cfg.tn;
+    p.init_est = init_est;
     if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
     if (m > 0 && cudaMemsetAsync(p.histo, 0, (size_t)m * sizeof(int), stream) != cudaSuccess)
         return -3;
@@ -101,9 +103,9 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
 }
 
 template int launch_histocore<int>(const int *, const int *, long long, long long, int *, void *,
-                                   LastResult *, cudaStream_t, const LaunchCfg &);
+                                   LastResult *, cudaStream_t, const LaunchCfg &, const int *);
 template int launch_histocore<long long>(const long long *, const int *, long long, long long,
                                          int *, void *, LastResult *, cudaStream_t,
-                                         const LaunchCfg &);
+                                         const LaunchCfg &, const int *);
 
 }  // namespace pico

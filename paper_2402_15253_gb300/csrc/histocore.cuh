@@ -104,6 +104,12 @@ struct Params {
     Ctrl *ctl;                    // status word (errors)
     bool zero_histo;
     Tuning tn;
+    // Start from min(init_est[v], deg v), at least 1, instead of the degrees
+    // (core maintenance); nullptr: the degrees, as Alg. 6. From any start the rounds
+    // end with cnt >= estimate everywhere, so the estimates are then a lower
+    // bound of the coreness, and the coreness itself when the start is an
+    // upper bound of it.
+    const int *init_est = nullptr;
 };
 
 __device__ __forceinline__ int kclass(int K) { return K <= kWarpK ? 0 : (K <= kBlockK ? 1 : 2); }
@@ -468,7 +474,12 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         if (v < n) {
             const Off r0 = p.rp[v];
             d = (long long)(p.rp[v + 1] - r0);
-            p.vinfo[v] = make_vrec<Off>((int)d, r0);
+            int e0 = (int)d;
+            if (p.init_est && d > 0) {   // a non-isolated vertex has coreness >= 1
+                const int x = ldcg(p.init_est + v);
+                e0 = x < 1 ? 1 : (x < e0 ? x : e0);
+            }
+            p.vinfo[v] = make_vrec<Off>(e0, r0);
             p.mv[0][v] = make_int2(0, 0);
             p.mv[1][v] = make_int2(0, 0);
         }

@@ -51,9 +51,11 @@ int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *
                    void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg,
                    int mode = 0);
 
+// init_est: start from these estimates (core maintenance; may alias core)
 template <typename Off>
 int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int *core,
-                     void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
+                     void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg,
+                     const int *init_est = nullptr);
 
 // the comparison baselines of Sec. V (ablation.cu)
 size_t gpp_ws_bytes(long long n, long long m);
@@ -92,11 +94,5 @@ int selftest_wait_timeout(LastResult *last, int limit_ms, cudaStream_t stream, c
 // (capi.cu); returns a pico_status.
 int current_device(LaunchCfg *cfg, LastResult **last);
 
-// Index2core (NbrCore) rounds from given estimates and a first active set
-// (core maintenance, dyn.cu); core may alias init_est.
-template <typename Off>
-int launch_index2core_from(const Off *rp, const int *ci, long long n, long long m, int *core,
-                           const int *init_est, const int *init_active, unsigned n_init,
-                           void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
 
 }  // namespace pico
