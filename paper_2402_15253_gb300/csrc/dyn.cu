@@ -355,7 +355,9 @@ __global__ void check_kernel(const int *T, const long long *ntp, const long long
 // ---------------------------------------------------------------------------
 namespace maint {
 
-enum : int { L_ALLB = 0, L_CS = 1, L_CB = 2, L_QS = 3, L_QB = 4, L_NC = 5, L_RAISED = 6 };
+enum : int {
+    L_ALLB = 0, L_CS = 1, L_CB = 2, L_QS = 3, L_QB = 4, L_NC = 5, L_RAISED = 6, L_RS = 7, L_RB = 8
+};
 
 struct Params {
     const long long *rp;
@@ -364,10 +366,10 @@ struct Params {
     int *core;             // in: a lower bound of the coreness; out: the coreness
     int *cd;               // neighbours of core >= own (0 at rest)
     int *sup;              // support of a candidate
-    unsigned char *flag;   // 1 candidate, 3 peeled candidate, 0 otherwise
+    unsigned char *flag;   // 1 candidate, 3 peeled candidate, 4 just raised, 0 otherwise
     int2 *allb;            // chunks of every large vertex
-    int *cs, *qs;          // candidates, peel queue (small vertices)
-    int2 *cb, *qb;         // their chunks
+    int *cs, *qs, *rs;     // candidates, peel queue, raised vertices (small vertices)
+    int2 *cb, *qb, *rb;    // their chunks
     unsigned cap;
     Ctrl *ctl;
     Tuning tn;
@@ -411,6 +413,35 @@ struct SupArc {
         if (one) {
             const int tot = __reduce_add_sync(kFull, mine);
             if ((threadIdx.x & 31) == 0 && tot) red_add(sup + vo[0], tot);
+        }
+    }
+};
+
+// after a pass: a raised vertex v recounts cd over its row with the new
+// values, and adds itself to the cd of its neighbours that were not raised and
+// sit at its new value (it now counts for them)
+struct RaiseArc {
+    static constexpr int kArcs = 4;
+    const int *core;
+    const unsigned char *flag;
+    int *cd;
+    unsigned long long n_arcs = 0;
+    __device__ __forceinline__ bool item(int v, int &a, int &)
+    {
+        a = ldcg(core + v);
+        return true;
+    }
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&vo)[kArcs],
+                                         const int (&u)[kArcs], const long long (&)[kArcs],
+                                         const int (&a)[kArcs], const int (&)[kArcs])
+    {
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            if (!valid[j]) continue;
+            ++n_arcs;
+            const int cu = ldcg(core + u[j]);
+            if (cu >= a[j]) red_add(cd + vo[j], 1);
+            if (cu == a[j] && __ldcg(flag + u[j]) != 4) red_add(cd + u[j], 1);
         }
     }
 };
@@ -490,18 +521,19 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
 
     for (int pass = 0; pass < p.max_passes; ++pass) {
         if (dom.leader()) {
-            for (int w = L_CS; w <= L_RAISED; ++w) live[w] = 0;
+            for (int w = L_CS; w <= L_RB; ++w) live[w] = 0;
         }
-        // A: cd = neighbours of core >= own, for every vertex
-        {
+        // A (first pass): cd = neighbours of core >= own, for every vertex;
+        // later passes keep it up to date from the raised vertices (G)
+        if (pass == 0) {
             i2c::CntArc<long long> f{p.core, p.cd};
             expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, p.allb, nallb, gwarp, nwarps, f,
                    p.tn);
             arcs += f.n_arcs;
             atomics += f.n_atomics;
+            if (!dom.sync()) return;
+            if (threadIdx.x == 0) ++st[kStBarriers];
         }
-        if (!dom.sync()) return;
-        if (threadIdx.x == 0) ++st[kStBarriers];
         // B: candidates
         for (long long base = first; base < n; base += nthreads) {
             const long long v = base + threadIdx.x;
@@ -511,7 +543,6 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
                 const int c = ldcg(p.core + v);
                 d = p.rp[v + 1] - p.rp[v];
                 cand = d >= c + 1 && ldcg(p.cd + v) >= c + 1;
-                p.cd[v] = 0;
                 p.sup[v] = 0;
                 p.flag[v] = cand ? 1 : 0;
             }
@@ -584,26 +615,38 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
             e0 = snap[L_QS];
             e1 = snap[L_QB];
         }
-        // F: the survivors rise by one; flags back to 0
+        // F: the survivors rise by one (flag 4, listed); other flags back to 0
         i2c::for_vertices(
             p.cs, ncs, p.cb, ncb, tid, nthreads, gwarp, nwarps,
             [&](bool ok, int v) {
                 bool up = false;
+                long long d = 0;
                 if (ok) {
                     up = __ldcg(p.flag + v) == 1;
-                    if (up) p.core[v] = ldcg(p.core + v) + 1;
-                    p.flag[v] = 0;
+                    if (up) {
+                        p.core[v] = ldcg(p.core + v) + 1;
+                        p.cd[v] = 0;
+                        d = p.rp[v + 1] - p.rp[v];
+                    }
+                    p.flag[v] = up ? 4 : 0;
                 }
+                warp_append_vertex(up, v, d, p.rs, &live[L_RS], (unsigned)n, p.rb, &live[L_RB],
+                                   p.cap, ctl, p.tn);
                 const unsigned c = __popc(__ballot_sync(kFull, up));
                 if ((threadIdx.x & 31) == 0 && c) atomicAdd(&live[L_RAISED], c);
             },
             [&](int v) {
                 if ((threadIdx.x & 31) == 0) {
-                    if (__ldcg(p.flag + v) == 1) {
+                    const bool up = __ldcg(p.flag + v) == 1;
+                    if (up) {
                         p.core[v] = ldcg(p.core + v) + 1;
+                        p.cd[v] = 0;
                         atomicAdd(&live[L_RAISED], 1u);
+                        if (!push_chunks(v, p.rp[v + 1] - p.rp[v], p.rb, &live[L_RB], p.cap,
+                                         p.tn.chunk))
+                            set_error(ctl, kErrNotConverged);
                     }
-                    p.flag[v] = 0;
+                    p.flag[v] = up ? 4 : 0;
                 }
             });
         if (!dom.sync()) return;
@@ -613,7 +656,30 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
             if (snap[L_RAISED]) ++st[kStRounds];
         }
         if (snap[L_RAISED] == 0) break;
-        if (pass + 1 == p.max_passes && threadIdx.x == 0) set_error(ctl, kErrNotConverged);
+        if (pass + 1 == p.max_passes) {
+            if (threadIdx.x == 0) set_error(ctl, kErrNotConverged);
+            return;
+        }
+        // G: cd brought up to date around the raised vertices, flags back to 0
+        {
+            const unsigned nrs = snap[L_RS], nrb = snap[L_RB];
+            RaiseArc f{p.core, p.flag, p.cd};
+            expand(p.rp, p.ci, p.rs, nrs, p.rb, nrb, gwarp, nwarps, f, p.tn,
+                   batch_width(nrs, nrb, nwarps));
+            arcs += f.n_arcs;
+            if (!dom.sync()) return;
+            if (threadIdx.x == 0) ++st[kStBarriers];
+            i2c::for_vertices(
+                p.rs, nrs, p.rb, nrb, tid, nthreads, gwarp, nwarps,
+                [&](bool ok, int v) {
+                    if (ok) p.flag[v] = 0;
+                },
+                [&](int v) {
+                    if ((threadIdx.x & 31) == 0) p.flag[v] = 0;
+                });
+            if (!dom.sync()) return;
+            if (threadIdx.x == 0) ++st[kStBarriers];
+        }
     }
 }
 
@@ -646,7 +712,8 @@ size_t maint_ws_bytes(long long n, long long m)
     c.take<unsigned char>(n);   // flag
     c.take<int>(n);             // cs
     c.take<int>(n);             // qs
-    for (int i = 0; i < 3; ++i) c.take<int2>(chunk_capacity(m));
+    c.take<int>(n);             // rs
+    for (int i = 0; i < 4; ++i) c.take<int2>(chunk_capacity(m));
     return c.size();
 }
 
@@ -849,10 +916,12 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
         p.flag = cw.take<unsigned char>(n);
         p.cs = cw.take<int>(n);
         p.qs = cw.take<int>(n);
+        p.rs = cw.take<int>(n);
         p.cap = (unsigned)pico::chunk_capacity(m_new);
         p.allb = cw.take<int2>(p.cap);
         p.cb = cw.take<int2>(p.cap);
         p.qb = cw.take<int2>(p.cap);
+        p.rb = cw.take<int2>(p.cap);
         p.tn = cfg.tn;
         p.max_passes = (int)std::min<long long>(n_ins + 1, 1ll << 30);
         ok = cudaMemsetAsync(p.ctl, 0, sizeof(pico::Ctrl), s) == cudaSuccess;
