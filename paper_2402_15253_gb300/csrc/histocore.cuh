@@ -317,6 +317,10 @@ __device__ __forceinline__ void sum_done(const Params<Off> &p, int par, unsigned
     list_changed(p, live, v, sum_apply(p, par, v, rs, K, h, sum, acc));
 }
 
+// Slots each thread reads per step of a warp or CTA walk (consecutive,
+// descending): a CTA step covers 4 x 512 slots, a warp step 4 x 32.
+constexpr int kWalkSlots = 4;
+
 // SumHisto by one CTA for a vertex with a large estimate.
 template <typename Off>
 __device__ void sum_block(const Params<Off> &p, int par, unsigned *live, int v, int *s,
@@ -327,10 +331,16 @@ __device__ void sum_block(const Params<Off> &p, int par, unsigned *live, int v, 
     const int K = (int)rec.x;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int carry = 0;
-    for (int top = K; top >= 1; top -= (int)blockDim.x) {
-        const int slot = top - (int)threadIdx.x;
-        const int val = slot >= 1 ? ldcg(p.histo + rs + slot - 1) : 0;
-        int inc = val;
+    for (int top = K; top >= 1; top -= kWalkSlots * (int)blockDim.x) {
+        const int s0 = top - kWalkSlots * (int)threadIdx.x;   // this thread: s0, s0 - 1, ...
+        int r[kWalkSlots], t = 0;
+#pragma unroll
+        for (int j = 0; j < kWalkSlots; ++j) {
+            const int slot = s0 - j;
+            t += slot >= 1 ? ldcg(p.histo + rs + slot - 1) : 0;
+            r[j] = t;
+        }
+        int inc = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(kFull, inc, o);
@@ -350,14 +360,22 @@ __device__ void sum_block(const Params<Off> &p, int par, unsigned *live, int v, 
             if (lane == 0) s[64] = INT_MAX;
         }
         __syncthreads();
-        const int run = carry + s[32 + warp] + inc;
-        if (slot >= 1 && run >= slot) atomicMin(&s[64], (int)threadIdx.x);
+        const int before = carry + s[32 + warp] + inc - t;   // slots above s0
+        int found = INT_MAX, frun = 0;
+#pragma unroll
+        for (int j = kWalkSlots - 1; j >= 0; --j)
+            if (s0 - j >= 1 && before + r[j] >= s0 - j) {
+                found = kWalkSlots * (int)threadIdx.x + j;
+                frun = before + r[j];
+            }
+        if (found != INT_MAX) atomicMin(&s[64], found);
         __syncthreads();
-        const int first = s[64];
+        const int first = s[64];   // the highest slot that qualifies
         if (first != INT_MAX) {
-            if ((int)threadIdx.x == first) {
+            if (first == found) {
+                const int slot = s0 - first % kWalkSlots;
                 slots += (unsigned long long)(K - slot + 1);
-                sum_done(p, par, live, v, rs, K, slot, run, acc);
+                sum_done(p, par, live, v, rs, K, slot, frun, acc);
             }
             __syncthreads();
             return;
@@ -378,26 +396,40 @@ __device__ __forceinline__ void sum_warp(const Params<Off> &p, int par, unsigned
     const Off rs = (Off)rec.y;
     const int K = (int)rec.x;
     int carry = 0;
-    for (int top = K; top >= 1; top -= 32) {
-        const int slot = top - lane;
-        const int val = slot >= 1 ? ldcg(p.histo + rs + slot - 1) : 0;
-        int inc = val;
+    for (int top = K; top >= 1; top -= 32 * kWalkSlots) {
+        const int s0 = top - kWalkSlots * lane;   // this lane: s0, s0 - 1, ...
+        int r[kWalkSlots], t = 0;
+#pragma unroll
+        for (int j = 0; j < kWalkSlots; ++j) {
+            const int slot = s0 - j;
+            t += slot >= 1 ? ldcg(p.histo + rs + slot - 1) : 0;
+            r[j] = t;
+        }
+        int inc = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(kFull, inc, o);
             if (lane >= o) inc += y;
         }
-        const int run = carry + inc;
-        const unsigned b = __ballot_sync(kFull, slot >= 1 && run >= slot);
+        const int before = carry + inc - t;   // slots above s0
+        int found = kWalkSlots, frun = 0;
+#pragma unroll
+        for (int j = kWalkSlots - 1; j >= 0; --j)
+            if (s0 - j >= 1 && before + r[j] >= s0 - j) {
+                found = j;
+                frun = before + r[j];
+            }
+        const unsigned b = __ballot_sync(kFull, found < kWalkSlots);
         if (b) {
-            const int L = __ffs(b) - 1;
+            const int L = __ffs(b) - 1;   // the lowest lane holds the highest slots
             if (lane == L) {
+                const int slot = s0 - found;
                 slots += (unsigned long long)(K - slot + 1);
-                sum_done(p, par, live, v, rs, K, slot, run, acc);
+                sum_done(p, par, live, v, rs, K, slot, frun, acc);
             }
             return;
         }
-        carry = __shfl_sync(kFull, run, 31);
+        carry += __shfl_sync(kFull, inc, 31);
     }
     if (lane == 0) set_error(p.ctl, kErrBadGraph);
 }
