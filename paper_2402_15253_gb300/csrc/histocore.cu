@@ -48,6 +48,7 @@ size_t histocore_ws_bytes(long long n, long long m)
     c.take<int>(n);        // us
     c.take<int2>(chunk_capacity(m));   // ub
     c.take<int2>(chunk_capacity(m));   // ib
+    c.take<unsigned char>((size_t)((n + 3) & ~3ll));   // cand
     return c.size();
 }
 
@@ -77,6 +78,7 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
     p.ub_cap = (unsigned)chunk_capacity(m);
     p.ub = c.take<int2>(p.ub_cap);
     p.ib = c.take<int2>(p.ub_cap);
+    p.cand = c.take<unsigned char>((size_t)((n + 3) & ~3ll));
     p.zero_histo = false;
     p.tn = cfg.tn;
     p.init_est = init_est;

@@ -45,6 +45,15 @@
 // round r-1's changed vertices in the other buffer (their lists are intact
 // until UpdateHisto of round r appends to them).
 //
+// Deferred V_cnt decision in pull rounds. Deciding the append at the edit
+// needs the old value of slot K, so every edit of slot K is an atomic whose
+// result the warp waits for before its next arcs. A pull round instead makes
+// every edit a reduction, marks the rows whose slot K it decremented (cand),
+// and after a barrier lists the marked u with histo[u][K] < K. The set is the
+// same: after SumHisto every vertex has cnt >= K (unchanged vertices kept it,
+// changed ones set it to a sum >= h), slot K only decreases in UpdateHisto,
+// so its count ends below K exactly when one decrement took it from K to K-1.
+//
 // Load balance. V_cnt is kept as three lists by the estimate K that SumHisto
 // will walk down from: K <= 32 one thread per vertex, K <= 2048 one warp per
 // vertex (32 slots per step, warp suffix scan), larger K one CTA per vertex.
@@ -110,6 +119,10 @@ struct Params {
     // bound of the coreness, and the coreness itself when the start is an
     // upper bound of it.
     const int *init_est = nullptr;
+    // Marks of the rows whose cnt slot a pull round decremented (n bytes,
+    // rounded up to 4; zero between rounds); nullptr: pull rounds decide the
+    // append at the edit, as push rounds do.
+    unsigned char *cand = nullptr;
 };
 
 __device__ __forceinline__ int kclass(int K) { return K <= kWarpK ? 0 : (K <= kBlockK ? 1 : 2); }
@@ -242,6 +255,7 @@ struct PullArc {
     int par;
     unsigned cap;
     int ymin;              // no row with K <= ymin can be edited
+    unsigned char *cand;   // row marks of the deferred V_cnt decision (nullptr: decide here)
     unsigned long long n_arcs = 0, n_atomics = 0;
 
     __device__ __forceinline__ bool item(int u, int &K, int &)
@@ -256,6 +270,20 @@ struct PullArc {
         int2 r[kArcs];
 #pragma unroll
         for (int j = 0; j < kArcs; ++j) r[j] = valid[j] ? __ldcg(mv + w[j]) : make_int2(0, 0);
+        if (cand) {   // reductions only; rows whose slot K fell are listed after the barrier
+#pragma unroll
+            for (int j = 0; j < kArcs; ++j) {
+                if (!valid[j]) continue;
+                ++n_arcs;
+                const int x = r[j].x, y = r[j].y;
+                if (x == 0 || K[j] <= y) continue;
+                n_atomics += 2;
+                red_add(histo + ru[j] + y - 1, 1);
+                red_add(histo + ru[j] + (x < K[j] ? x : K[j]) - 1, -1);
+                if (x >= K[j]) cand[uu[j]] = 1;
+            }
+            return;
+        }
         bool push[kArcs];
 #pragma unroll
         for (int j = 0; j < kArcs; ++j) {
@@ -268,6 +296,39 @@ struct PullArc {
         append_vcnt(push, uu, K, live_base + 3 * par, tl, wl, bl, cap, ctl);
     }
 };
+
+// Deferred V_cnt decision of a pull round (after its barrier): every marked
+// row u with histo[u][K] < K joins V_cnt of parity np; the marks are cleared.
+// Each thread takes 4 vertices (one 32-bit word of marks) per step; the up to
+// 3 padding bytes past n are never set by an edit and only cleared here.
+template <typename Off>
+__device__ __forceinline__ void collect_vcnt(const Params<Off> &p, unsigned *live, int np,
+                                             unsigned tid, unsigned nthreads)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const long long n = p.n, ngroups = (n + 3) >> 2;
+    unsigned *const words = reinterpret_cast<unsigned *>(p.cand);
+    for (long long base = (long long)(tid - lane); base < ngroups; base += nthreads) {
+        const long long g = base + lane;
+        const unsigned marks = g < ngroups ? __ldcg(words + g) : 0u;
+        if (!__any_sync(kFull, marks != 0u)) continue;
+        if (marks) words[g] = 0u;
+        bool in[4];
+        int vtx[4], K[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            vtx[j] = (int)(4 * g + j);
+            in[j] = false;
+            K[j] = 0;
+            if (vtx[j] < n && ((marks >> (8 * j)) & 0xffu)) {   // the padding is never a row
+                const VRec<Off> rec = __ldcg(p.vinfo + vtx[j]);
+                K[j] = (int)rec.x;
+                in[j] = ldcg(p.histo + (Off)rec.y + K[j] - 1) < K[j];
+            }
+        }
+        append_vcnt(in, vtx, K, live + 3 * np, p.tl[np], p.wl[np], p.bl[np], (unsigned)n, p.ctl);
+    }
+}
 
 // Per-thread totals of the vertices a thread changed in SumHisto.
 struct RoundAcc {
@@ -514,6 +575,7 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
             p.vinfo[v] = make_vrec<Off>(e0, r0);
             p.mv[0][v] = make_int2(0, 0);
             p.mv[1][v] = make_int2(0, 0);
+            if (p.cand) p.cand[v] = 0;
         }
         const unsigned nch =
             d > p.tn.small_deg ? (unsigned)((d + p.tn.chunk - 1) / p.tn.chunk) : 0u;
@@ -635,13 +697,18 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         const bool pull = pull_round(p, vol);
         if (pull) {
             PullArc<Off> f{p.vinfo, p.mv[par], p.histo, p.tl[np], p.wl[np], p.bl[np],
-                           ctl,     live,      np,      (unsigned)n, ymin};
+                           ctl,     live,      np,      (unsigned)n, ymin,    p.cand};
             expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, ilist, nib, gwarp, nwarps, f,
                    p.tn, batch_width((unsigned)n, nib, nwarps));
             arcs += acc.arcs;
             pulled += f.n_arcs;
             atomics += f.n_atomics;
             if (threadIdx.x == 0) ++st[kStPullRounds];
+            if (p.cand) {   // all edits in place: list the rows whose cnt fell below K
+                if (!dom.sync()) return;
+                if (threadIdx.x == 0) ++st[kStBarriers];
+                collect_vcnt(p, live, np, tid, nthreads);
+            }
         } else {
             UpdateArc<Off> f{p.vinfo, p.mv[par], p.histo, p.tl[np], p.wl[np], p.bl[np],
                              ctl,     live,      np,      (unsigned)n};

@@ -127,6 +127,7 @@ int launch_hybrid(const Off *rp, const int *ci, long long n, long long m, int *c
         hp.ub_cap = (unsigned)chunk_capacity(m);
         hp.ub = c.take<int2>(hp.ub_cap);
         hp.ib = c.take<int2>(hp.ub_cap);
+        hp.cand = c.take<unsigned char>((size_t)((n + 3) & ~3ll));
         hp.zero_histo = true;   // cleared in the kernel, only when HistoCore runs
         hp.tn = cfg.tn;
     }
