@@ -43,6 +43,8 @@ size_t histocore_ws_bytes(long long n, long long m)
     c.take<longlong2>(n);  // vinfo (sized for int64 offsets)
     c.take<int2>(n);       // mv[0]
     c.take<int2>(n);       // mv[1]
+    c.take<unsigned>(n);   // mvp[0]
+    c.take<unsigned>(n);   // mvp[1]
     c.take<int>(m);        // histo
     for (int i = 0; i < 6; ++i) c.take<int>(n);
     c.take<int>(n);        // us
@@ -68,6 +70,8 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
     p.vinfo = reinterpret_cast<histo::VRec<Off> *>(c.take<longlong2>(n));
     p.mv[0] = c.take<int2>(n);
     p.mv[1] = c.take<int2>(n);
+    p.mvp[0] = c.take<unsigned>(n);
+    p.mvp[1] = c.take<unsigned>(n);
     p.histo = c.take<int>(m);
     for (int i = 0; i < 2; ++i) {
         p.tl[i] = c.take<int>(n);

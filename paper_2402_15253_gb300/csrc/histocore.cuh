@@ -43,7 +43,10 @@
 // kept per round parity (mv[r & 1]) so that pulling rows can tell whether a
 // neighbour changed in this round; SumHisto of round r clears the entries of
 // round r-1's changed vertices in the other buffer (their lists are intact
-// until UpdateHisto of round r appends to them).
+// until UpdateHisto of round r appends to them). Pulling rows gather the
+// record of every neighbour, so a packed copy (mvp: old << 16 | new in one
+// word, half the bytes of mv) is what they read; estimates above 65534 store
+// a sentinel that sends the reader to mv.
 //
 // Deferred V_cnt decision in pull rounds. Deciding the append at the edit
 // needs the old value of slot K, so every edit of slot K is an atomic whose
@@ -53,6 +56,13 @@
 // same: after SumHisto every vertex has cnt >= K (unchanged vertices kept it,
 // changed ones set it to a sum >= h), slot K only decreases in UpdateHisto,
 // so its count ends below K exactly when one decrement took it from K to K-1.
+//
+// Neighbour gathers (the estimates in InitHisto and push rounds, the packed
+// records in pull rounds) go through L1 (ld.global.ca): on skewed graphs most
+// arcs end at a few hubs, whose records then hit in L1. These arrays are not
+// written during the phases that gather them, and every grid barrier ends
+// with an acquire at GPU scope, after which a weak load observes every write
+// made before the barrier, so no line cached in an earlier phase is read.
 //
 // Load balance. V_cnt is kept as three lists by the estimate K that SumHisto
 // will walk down from: K <= 32 one thread per vertex, K <= 2048 one warp per
@@ -103,6 +113,8 @@ struct Params {
     VRec<Off> *vinfo;             // n records {estimate, histogram base}
     int2 *mv[2];                  // per round parity: {old, new} estimate of the vertices
                                   // changed in that round, {0, 0} for the others
+    unsigned *mvp[2] = {nullptr, nullptr};   // the same records packed (kMvpWide: read mv),
+                                             // 0 for the others; nullptr: pull rounds read mv
     int *histo;                   // m slots (zeroed by run() when zero_histo)
     int *tl[2], *wl[2], *bl[2];   // V_cnt lists by class, per parity (n slots each)
     int *us;                      // changed vertices of small degree
@@ -125,6 +137,14 @@ struct Params {
     unsigned char *cand = nullptr;
 };
 
+// Packed {old, new} record: old << 16 | new when old <= 65534 (new < old);
+// kMvpWide otherwise (never a packed value, since new < old).
+constexpr unsigned kMvpWide = 0xffffffffu;
+__device__ __forceinline__ unsigned pack_mv(int x, int y)
+{
+    return x <= 0xfffe ? ((unsigned)x << 16) | (unsigned)y : kMvpWide;
+}
+
 __device__ __forceinline__ int kclass(int K) { return K <= kWarpK ? 0 : (K <= kBlockK ? 1 : 2); }
 
 template <typename Off>
@@ -144,7 +164,7 @@ struct InitArc {
     {
         int du[kArcs];
 #pragma unroll
-        for (int j = 0; j < kArcs; ++j) du[j] = valid[j] ? (int)__ldcg(vinfo + u[j]).x : 0;
+        for (int j = 0; j < kArcs; ++j) du[j] = valid[j] ? (int)__ldca(vinfo + u[j]).x : 0;
 #pragma unroll
         for (int j = 0; j < kArcs; ++j)
             if (valid[j]) {
@@ -223,7 +243,7 @@ struct UpdateArc {
 #pragma unroll
         for (int j = 0; j < kArcs; ++j) {
             VRec<Off> r = make_vrec<Off>(0, 0);
-            if (valid[j]) r = __ldcg(vinfo + u[j]);
+            if (valid[j]) r = __ldca(vinfo + u[j]);
             K[j] = (int)r.x;
             ru[j] = (Off)r.y;
         }
@@ -256,6 +276,7 @@ struct PullArc {
     unsigned cap;
     int ymin;              // no row with K <= ymin can be edited
     unsigned char *cand;   // row marks of the deferred V_cnt decision (nullptr: decide here)
+    const unsigned *mvp;   // packed records of this round (nullptr: gather mv)
     unsigned long long n_arcs = 0, n_atomics = 0;
 
     __device__ __forceinline__ bool item(int u, int &K, int &)
@@ -268,8 +289,18 @@ struct PullArc {
                                          const int (&K)[kArcs], const int (&)[kArcs])
     {
         int2 r[kArcs];
+        if (mvp) {
+            unsigned q[kArcs];
 #pragma unroll
-        for (int j = 0; j < kArcs; ++j) r[j] = valid[j] ? __ldcg(mv + w[j]) : make_int2(0, 0);
+            for (int j = 0; j < kArcs; ++j) q[j] = valid[j] ? __ldca(mvp + w[j]) : 0u;
+#pragma unroll
+            for (int j = 0; j < kArcs; ++j)
+                r[j] = q[j] == kMvpWide ? __ldcg(mv + w[j])
+                                        : make_int2((int)(q[j] >> 16), (int)(q[j] & 0xffffu));
+        } else {
+#pragma unroll
+            for (int j = 0; j < kArcs; ++j) r[j] = valid[j] ? __ldcg(mv + w[j]) : make_int2(0, 0);
+        }
         if (cand) {   // reductions only; rows whose slot K fell are listed after the barrier
 #pragma unroll
             for (int j = 0; j < kArcs; ++j) {
@@ -349,6 +380,7 @@ __device__ __forceinline__ long long sum_apply(const Params<Off> &p, int par, in
     }
     p.vinfo[v].x = h;
     p.mv[par][v] = make_int2(K, h);
+    if (p.mvp[par]) p.mvp[par][v] = pack_mv(K, h);
     p.histo[rs + h - 1] = sum;
     const long long d = (long long)(p.rp[v + 1] - rs);
     acc.arcs += (unsigned long long)d;
@@ -575,6 +607,10 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
             p.vinfo[v] = make_vrec<Off>(e0, r0);
             p.mv[0][v] = make_int2(0, 0);
             p.mv[1][v] = make_int2(0, 0);
+            if (p.mvp[0]) {
+                p.mvp[0][v] = 0u;
+                p.mvp[1][v] = 0u;
+            }
             if (p.cand) p.cand[v] = 0;
         }
         const unsigned nch =
@@ -650,6 +686,7 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
                                  : (k < pt + pw ? ldcg(p.wl[np] + (k - pt))
                                                 : ldcg(p.bl[np] + (k - pt - pw)));
             p.mv[np][v] = make_int2(0, 0);
+            if (p.mvp[np]) p.mvp[np][v] = 0u;
         }
         // SumHisto: CTA items, then warp items, then thread items
         RoundAcc acc;
@@ -697,7 +734,8 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         const bool pull = pull_round(p, vol);
         if (pull) {
             PullArc<Off> f{p.vinfo, p.mv[par], p.histo, p.tl[np], p.wl[np], p.bl[np],
-                           ctl,     live,      np,      (unsigned)n, ymin,    p.cand};
+                           ctl,     live,      np,      (unsigned)n, ymin,    p.cand,
+                           p.mvp[par]};
             expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, ilist, nib, gwarp, nwarps, f,
                    p.tn, batch_width((unsigned)n, nib, nwarps));
             arcs += acc.arcs;

@@ -117,6 +117,8 @@ int launch_hybrid(const Off *rp, const int *ci, long long n, long long m, int *c
         hp.vinfo = reinterpret_cast<histo::VRec<Off> *>(c.take<longlong2>(n));
         hp.mv[0] = c.take<int2>(n);
         hp.mv[1] = c.take<int2>(n);
+        hp.mvp[0] = c.take<unsigned>(n);
+        hp.mvp[1] = c.take<unsigned>(n);
         hp.histo = c.take<int>(m);
         for (int i = 0; i < 2; ++i) {
             hp.tl[i] = c.take<int>(n);

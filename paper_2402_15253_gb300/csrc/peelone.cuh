@@ -22,6 +22,14 @@
 //           the level's queue is written back to k. Values seen in between
 //           are only compared against k, where a dip below k and k itself
 //           give the same answer.
+// The guard read goes through L1 (most arcs of a skewed graph end at a few
+// hubs). An L1 line can be older than L2 within a level, but the estimates of
+// unqueued vertices only decrease, so an old value is never below the current
+// one: it can only send a thread to an atomic that finds u already at k (an
+// overshoot, handled as above), never skip a needed decrement. Vertices of
+// earlier levels are at most k - 1 in every copy, and repaired values are
+// compared only after the barrier that ends the level, whose acquire makes
+// L1 loads observe them.
 // Every vertex is queued exactly once over the whole run (only one thread can
 // move it from k + 1 to k), so the queue is the peel order and needs n slots.
 //
@@ -82,7 +90,7 @@ struct Arc {
     {
         int c[kArcs], old[kArcs];
 #pragma unroll
-        for (int j = 0; j < kArcs; ++j) c[j] = valid[j] ? ldcg(core + u[j]) : 0;
+        for (int j = 0; j < kArcs; ++j) c[j] = valid[j] ? __ldca(core + u[j]) : 0;
 #pragma unroll
         for (int j = 0; j < kArcs; ++j) {
             old[j] = 0;
