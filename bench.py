@@ -471,12 +471,14 @@ def bench_auto(pico, rp, ci, n, arcs, ref, stream, reps=3):
             "method": {v: k for k, v in pico.ALGOS.items()}[chose]}
 
 
-def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6):
+def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6,
+                      update_tuning=None, recompute_tuning=None):
     """Core maintenance on the workload graph: batches of k random edge
     insertions (non-edges), k random deletions (existing edges) and both,
     each timed with CUDA events around pico_dyn_update, against a full
     recomputation (PICO_ALGO_AUTO) of the updated graph. The maintained
-    coreness must equal the recomputed one."""
+    coreness must equal the recomputed one. The tunings (S, C, T, K) are set
+    before each update and each recomputation (None: leave as is)."""
     import numpy as np
     import torch
     import graphgen as gg
@@ -532,6 +534,8 @@ def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6):
     for name, (bi, bd) in batches.items():
         ti = torch.tensor(bi, dtype=torch.int32, device=dev).reshape(-1, 2) if bi else None
         td = torch.tensor(bd, dtype=torch.int32, device=dev).reshape(-1, 2) if bd else None
+        if update_tuning:
+            pico.pico_set_tuning(*update_tuning)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -542,6 +546,8 @@ def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6):
             raise pico.PicoError(rc, "pico_dyn_update")
         st = pico.pico_get_stats(stream)
         rp2, ci2 = dg.csr()
+        if recompute_tuning:
+            pico.pico_set_tuning(*recompute_tuning)
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r0.record(stream)
         full = pico.coreness(rp2, ci2, "auto")
@@ -552,7 +558,8 @@ def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6):
         res["runs"][name] = {"update_ms": e0.elapsed_time(e1),
                              "recompute_ms": r0.elapsed_time(r1),
                              "speedup": r0.elapsed_time(r1) / e0.elapsed_time(e1),
-                             "stats": {x: st[x] for x in ("algo", "rounds", "frontier", "active")}}
+                             "stats": {x: st[x] for x in ("algo", "rounds", "frontier", "active", "subrounds",
+                                                             "barriers", "arcs", "atomics")}}
     dg.close()
     return res
 
@@ -843,7 +850,9 @@ def main():
                                             {a: statistics.median(v) for a, v in per.items()},
                                             stream)
     if rank == 0 and not args.no_maintenance:
-        line["maintenance"] = bench_maintenance(pico, g, stream)
+        line["maintenance"] = bench_maintenance(
+            pico, g, stream, update_tuning=tuned["histocore"],
+            recompute_tuning=tuned[line["auto"]["method"]] if rank == 0 else None)
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)
     if rank == 0 and args.serve_requests > 0:

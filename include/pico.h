@@ -313,8 +313,9 @@ int pico_get_tuning(int *small_deg, int *chunk, int *batched_threads, int *clust
  * PICO_ERR_INVALID_ARG (bad sizes, too little capacity) or a device status.
  * After an update with insertions, pico_get_stats describes the insertion
  * passes (algo PICO_STATS_MAINTENANCE: rounds = passes that raised a vertex,
- * frontier = vertices raised, active = candidates); otherwise the HistoCore
- * rounds of the deletions (algo PICO_ALGO_HISTOCORE).
+ * frontier = vertices raised, active = vertices of the passes' regions, the
+ * candidates connected to the inserted edges or to the last raised vertices);
+ * otherwise the HistoCore rounds of the deletions (algo PICO_ALGO_HISTOCORE).
  *
  * pico_dyn_coreness copies the current coreness (n int32) to device memory;
  * pico_dyn_graph exposes the current CSR (device pointers owned by the state,

@@ -364,7 +364,7 @@ struct Params {
     const int *ci;
     long long n, m;
     int *core;             // in: a lower bound of the coreness; out: the coreness
-    int *cd;               // neighbours of core >= own (0 at rest)
+    int *cd;               // neighbours of core >= own (exact for the final cores on return)
     int *sup;              // support of a candidate
     unsigned char *flag;   // 1 candidate, 3 peeled candidate, 4 just raised, 0 otherwise
     int2 *allb;            // chunks of every large vertex
@@ -374,6 +374,92 @@ struct Params {
     Ctrl *ctl;
     Tuning tn;
     int max_passes;
+    const int *ins;         // the batch's inserted edges (pairs): the first pass's seeds
+    long long n_ins;
+    int *reg;               // 1 while in the current pass's region (0 at rest)
+    int max_depth;          // region levels before falling back to every candidate
+    bool cd_valid;          // cd holds the counts of the graph without the inserted
+                            // edges (which are added here) instead of being counted
+    bool count_only;        // count cd over all arcs and stop
+};
+
+// Lists x in the current pass's region when pred holds and x is a candidate
+// not listed yet. Called by all 32 lanes together.
+__device__ __forceinline__ void visit(bool pred, int x, const long long *rp,
+                                      const unsigned char *flag, int *reg, int *cs, int2 *cb,
+                                      unsigned *live, unsigned n, unsigned cap, Ctrl *ctl,
+                                      const Tuning &tn)
+{
+    bool fresh = false;
+    long long d = 0;
+    if (pred && __ldcg(flag + x) == 1) fresh = atomicCAS(reg + x, 0, 1) == 0;
+    if (fresh) d = rp[x + 1] - rp[x];
+    warp_append_vertex(fresh, x, d, cs, &live[L_CS], n, cb, &live[L_CB], cap, ctl, tn);
+    const unsigned c = __popc(__ballot_sync(kFull, fresh));
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&live[L_NC], c);
+}
+
+// region growth: the candidate neighbours of a listed vertex at its own core
+// (same_core), or every candidate neighbour of a vertex raised in the previous
+// pass (the seeds of a later pass)
+struct GrowArc {
+    static constexpr int kArcs = 4;
+    const long long *rp;
+    const int *core;
+    const unsigned char *flag;
+    int *sup;              // support, counted on the way (same_core), as SupArc does
+    int *reg;
+    int *cs;
+    int2 *cb;
+    unsigned *live;
+    unsigned n, cap;
+    Ctrl *ctl;
+    Tuning tn;
+    bool same_core;
+    unsigned long long n_arcs = 0;
+    __device__ __forceinline__ bool item(int v, int &a, int &)
+    {
+        a = ldcg(core + v);
+        return true;
+    }
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&vo)[kArcs],
+                                         const int (&u)[kArcs], const long long (&)[kArcs],
+                                         const int (&a)[kArcs], const int (&)[kArcs])
+    {
+        bool take[kArcs], s[kArcs];
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            take[j] = false;
+            s[j] = false;
+            if (valid[j]) {
+                const bool fc = __ldcg(flag + u[j]) == 1;
+                if (same_core) {
+                    const int cu = ldcg(core + u[j]);
+                    take[j] = fc && cu == a[j];
+                    s[j] = cu > a[j] || take[j];
+                } else {
+                    take[j] = fc;
+                }
+            }
+            n_arcs += valid[j];
+        }
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j)
+            visit(take[j], u[j], rp, flag, reg, cs, cb, live, n, cap, ctl, tn);
+        if (!same_core) return;
+        const bool one = __all_sync(kFull, vo[0] == __shfl_sync(kFull, vo[0], 0) &&
+                                               vo[kArcs - 1] == vo[0]);
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            if (one) mine += s[j];
+            else if (s[j]) red_add(sup + vo[j], 1);
+        }
+        if (one) {
+            const int tot = __reduce_add_sync(kFull, mine);
+            if ((threadIdx.x & 31) == 0 && tot) red_add(sup + vo[0], tot);
+        }
+    }
 };
 
 // support: neighbours of higher core, or of equal core that are candidates
@@ -504,8 +590,9 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
         long long d = 0;
         if (v < n) {
             d = p.rp[v + 1] - p.rp[v];
-            p.cd[v] = 0;
+            if (!p.cd_valid) p.cd[v] = 0;
             p.flag[v] = 0;
+            p.reg[v] = 0;
         }
         const unsigned nch =
             d > p.tn.small_deg ? (unsigned)((d + p.tn.chunk - 1) / p.tn.chunk) : 0u;
@@ -515,9 +602,21 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
         else if (nch)
             set_error(ctl, kErrNotConverged);
     }
+    if (p.cd_valid) {   // the inserted arcs join the counts
+        for (long long i = tid; i < p.n_ins; i += nthreads) {
+            const int a = ldcg(p.ins + 2 * i), b = ldcg(p.ins + 2 * i + 1);
+            const int ca = ldcg(p.core + a), cb = ldcg(p.core + b);
+            if (cb >= ca) red_add(p.cd + a, 1);
+            if (ca >= cb) red_add(p.cd + b, 1);
+        }
+    }
     if (!dom.sync()) return;
     if (threadIdx.x == 0) ++st[kStBarriers];
     const unsigned nallb = snap[L_ALLB];
+    unsigned prs = 0, prb = 0;   // vertices raised in the previous pass (rs, rb)
+    auto visit_p = [&](bool pred, int x) {
+        visit(pred, x, p.rp, p.flag, p.reg, p.cs, p.cb, live, (unsigned)n, p.cap, ctl, p.tn);
+    };
 
     for (int pass = 0; pass < p.max_passes; ++pass) {
         if (dom.leader()) {
@@ -525,7 +624,7 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
         }
         // A (first pass): cd = neighbours of core >= own, for every vertex;
         // later passes keep it up to date from the raised vertices (G)
-        if (pass == 0) {
+        if (pass == 0 && !p.cd_valid) {
             i2c::CntArc<long long> f{p.core, p.cd};
             expand(p.rp, p.ci, (const int *)nullptr, (unsigned)n, p.allb, nallb, gwarp, nwarps, f,
                    p.tn);
@@ -533,40 +632,105 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
             atomics += f.n_atomics;
             if (!dom.sync()) return;
             if (threadIdx.x == 0) ++st[kStBarriers];
+            if (p.count_only) return;
         }
-        // B: candidates
+        // B: candidates (flag 1)
         for (long long base = first; base < n; base += nthreads) {
             const long long v = base + threadIdx.x;
-            long long d = 0;
-            bool cand = false;
             if (v < n) {
                 const int c = ldcg(p.core + v);
-                d = p.rp[v + 1] - p.rp[v];
-                cand = d >= c + 1 && ldcg(p.cd + v) >= c + 1;
+                const long long d = p.rp[v + 1] - p.rp[v];
                 p.sup[v] = 0;
-                p.flag[v] = cand ? 1 : 0;
+                p.flag[v] = d >= c + 1 && ldcg(p.cd + v) >= c + 1 ? 1 : 0;
             }
-            warp_append_vertex(cand, (int)v, d, p.cs, &live[L_CS], (unsigned)n, p.cb,
-                               &live[L_CB], p.cap, ctl, p.tn);
-            const unsigned c = __popc(__ballot_sync(kFull, cand));
-            if ((threadIdx.x & 31) == 0 && c) atomicAdd(&live[L_NC], c);
         }
         if (!dom.sync()) return;
-        if (threadIdx.x == 0) {
-            ++st[kStBarriers];
-            st[kStActive] += snap[L_NC];
-        }
-        if (snap[L_NC] == 0) break;
-        const unsigned ncs = snap[L_CS], ncb = snap[L_CB];
-        // C: support of the candidates
-        {
-            SupArc f{p.core, p.flag, p.sup};
-            expand(p.rp, p.ci, p.cs, ncs, p.cb, ncb, gwarp, nwarps, f, p.tn,
-                   batch_width(ncs, ncb, nwarps));
+        if (threadIdx.x == 0) ++st[kStBarriers];
+        // Region of the pass: the candidates connected to a seed through
+        // candidates of equal core, listed in cs / cb. Seeds: in the first
+        // pass the endpoints of the inserted edges (of an edge between
+        // different cores only the lower end, which is the only one whose
+        // count at its own core it raises); later, the vertices raised in the
+        // previous pass and their neighbours. Every component T of survivors
+        // at core c holds a seed:
+        //  - later passes: without one, T and its neighbours had the same
+        //    cores and T the same support in the previous pass, whose region
+        //    (by induction) held T's component, so T would have risen then;
+        //  - first pass: without one, T's support comes from edges that were
+        //    in the graph before the batch, towards T and vertices of core
+        //    >= c + 1, which were already in the old (c+1)-core (deletions
+        //    only lower cores). So T lay in the old (c+1)-core. With
+        //    insertions alone the cores are the old coreness, a contradiction.
+        //    After deletions in the same batch, the cores are what HistoCore
+        //    reached from min(old core, degree): the greatest estimates below
+        //    that start that no count contradicts, and raising T to c + 1
+        //    stays below the start and contradicts no count, another
+        //    contradiction.
+        if (pass == 0) {
+            for (long long base = (long long)(tid - (tid & 31)); base < p.n_ins; base += nthreads) {
+                const long long i = base + (tid & 31);
+                const bool ok = i < p.n_ins;
+                const int a = ok ? ldcg(p.ins + 2 * i) : 0, b = ok ? ldcg(p.ins + 2 * i + 1) : 0;
+                const int ca = ok ? ldcg(p.core + a) : 0, cb = ok ? ldcg(p.core + b) : 0;
+                visit_p(ok && cb >= ca, a);
+                visit_p(ok && ca >= cb, b);
+            }
+        } else {
+            i2c::for_vertices(
+                p.rs, prs, p.rb, prb, tid, nthreads, gwarp, nwarps,
+                [&](bool ok, int v) { visit_p(ok, v); },
+                [&](int v) { visit_p((threadIdx.x & 31) == 0, v); });
+            GrowArc f{p.rp, p.core, p.flag, p.sup, p.reg, p.cs, p.cb, live, (unsigned)n, p.cap,
+                      ctl,  p.tn,   false};
+            expand(p.rp, p.ci, p.rs, prs, p.rb, prb, gwarp, nwarps, f, p.tn,
+                   batch_width(prs, prb, nwarps));
             arcs += f.n_arcs;
         }
         if (!dom.sync()) return;
         if (threadIdx.x == 0) ++st[kStBarriers];
+        // The search scans the arcs of every vertex it lists once and counts
+        // its support on the way; x0 / x1 end the prefix of cs / cb so scanned.
+        unsigned x0 = 0, x1 = 0;
+        {
+            unsigned g0 = 0, g1 = 0, h0 = snap[L_CS], h1 = snap[L_CB];
+            int depth = 0;
+            while (g0 < h0 || g1 < h1) {
+                if (++depth > p.max_depth) {   // a long chain: take every candidate
+                    for (long long base = first; base < n; base += nthreads) {
+                        const long long v = base + threadIdx.x;
+                        visit_p(v < n, (int)v);
+                    }
+                    if (!dom.sync()) return;
+                    if (threadIdx.x == 0) ++st[kStBarriers];
+                    break;
+                }
+                GrowArc f{p.rp, p.core, p.flag, p.sup, p.reg, p.cs, p.cb, live, (unsigned)n, p.cap,
+                          ctl,  p.tn,   true};
+                expand(p.rp, p.ci, p.cs + g0, h0 - g0, p.cb + g1, h1 - g1, gwarp, nwarps, f,
+                       p.tn, batch_width(h0 - g0, h1 - g1, nwarps));
+                arcs += f.n_arcs;
+                if (!dom.sync()) return;
+                if (threadIdx.x == 0) ++st[kStBarriers];
+                g0 = h0;
+                g1 = h1;
+                h0 = snap[L_CS];
+                h1 = snap[L_CB];
+            }
+            x0 = g0;
+            x1 = g1;
+        }
+        if (threadIdx.x == 0) st[kStActive] += snap[L_NC];
+        if (snap[L_NC] == 0) break;   // no seeded component: nothing can rise
+        const unsigned ncs = snap[L_CS], ncb = snap[L_CB];
+        // C: support of the listed vertices the search did not scan
+        if (x0 < ncs || x1 < ncb) {
+            SupArc f{p.core, p.flag, p.sup};
+            expand(p.rp, p.ci, p.cs + x0, ncs - x0, p.cb + x1, ncb - x1, gwarp, nwarps, f, p.tn,
+                   batch_width(ncs - x0, ncb - x1, nwarps));
+            arcs += f.n_arcs;
+            if (!dom.sync()) return;
+            if (threadIdx.x == 0) ++st[kStBarriers];
+        }
         // D: the candidates without enough support start the peel
         i2c::for_vertices(
             p.cs, ncs, p.cb, ncb, tid, nthreads, gwarp, nwarps,
@@ -629,6 +793,7 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
                         d = p.rp[v + 1] - p.rp[v];
                     }
                     p.flag[v] = up ? 4 : 0;
+                    p.reg[v] = 0;
                 }
                 warp_append_vertex(up, v, d, p.rs, &live[L_RS], (unsigned)n, p.rb, &live[L_RB],
                                    p.cap, ctl, p.tn);
@@ -647,6 +812,7 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
                             set_error(ctl, kErrNotConverged);
                     }
                     p.flag[v] = up ? 4 : 0;
+                    p.reg[v] = 0;
                 }
             });
         if (!dom.sync()) return;
@@ -663,6 +829,8 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
         // G: cd brought up to date around the raised vertices, flags back to 0
         {
             const unsigned nrs = snap[L_RS], nrb = snap[L_RB];
+            prs = nrs;
+            prb = nrb;
             RaiseArc f{p.core, p.flag, p.cd};
             expand(p.rp, p.ci, p.rs, nrs, p.rb, nrb, gwarp, nwarps, f, p.tn,
                    batch_width(nrs, nrb, nwarps));
@@ -707,12 +875,12 @@ size_t maint_ws_bytes(long long n, long long m)
 {
     Carver c(nullptr);
     c.take<Ctrl>(1);
-    c.take<int>(n);             // cd
     c.take<int>(n);             // sup
     c.take<unsigned char>(n);   // flag
     c.take<int>(n);             // cs
     c.take<int>(n);             // qs
     c.take<int>(n);             // rs
+    c.take<int>(n);             // reg
     for (int i = 0; i < 4; ++i) c.take<int2>(chunk_capacity(m));
     return c.size();
 }
@@ -730,6 +898,8 @@ struct pico_dyn {
     int *ci[2];
     int cur;
     int *core;
+    int *cd;         // per vertex: neighbours of core >= own (insertion passes)
+    bool cd_valid;   // cd matches the current graph and coreness
 };
 
 namespace {
@@ -754,6 +924,60 @@ int sync_status(cudaStream_t s)
 
 extern "C" {
 
+namespace {
+
+// Carves the insertion passes' scratch from ws (maint_ws_bytes) and launches
+// them on the state's current graph, or only the count of cd (count_only).
+bool launch_maint(pico_dyn *d, const long long *rp, const int *ci, long long m, const int32_t *ins,
+                  long long n_ins, bool cd_valid, bool count_only, void *ws,
+                  cudaStream_t s, const pico::LaunchCfg &cfg, pico::LastResult *last)
+{
+    const long long n = d->n;
+    pico::dyn::maint::Params p{};
+    pico::Carver cw(ws);
+    p.rp = rp;
+    p.ci = ci;
+    p.n = n;
+    p.m = m;
+    p.core = d->core;
+    p.cd = d->cd;
+    p.ctl = cw.take<pico::Ctrl>(1);
+    p.sup = cw.take<int>(n);
+    p.flag = cw.take<unsigned char>(n);
+    p.cs = cw.take<int>(n);
+    p.qs = cw.take<int>(n);
+    p.rs = cw.take<int>(n);
+    p.reg = cw.take<int>(n);
+    p.cap = (unsigned)pico::chunk_capacity(m);
+    p.allb = cw.take<int2>(p.cap);
+    p.cb = cw.take<int2>(p.cap);
+    p.qb = cw.take<int2>(p.cap);
+    p.rb = cw.take<int2>(p.cap);
+    p.tn = cfg.tn;
+    p.max_passes = (int)std::min<long long>(n_ins + 1, 1ll << 30);
+    p.ins = ins;
+    p.n_ins = n_ins;
+    p.max_depth = 128;
+    p.cd_valid = cd_valid;
+    p.count_only = count_only;
+    if (cudaMemsetAsync(p.ctl, 0, sizeof(pico::Ctrl), s) != cudaSuccess) return false;
+    static int occ[64] = {};
+    int &o = occ[cfg.device & 63];
+    if (o == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pico::dyn::maint::maint_kernel,
+                                                       pico::kThreads, 0) != cudaSuccess ||
+         o <= 0))
+        return false;
+    const int per_sm = o < cfg.max_blocks_per_sm ? o : cfg.max_blocks_per_sm;
+    unsigned long long limit = cfg.limit_ns;
+    void *args[] = {&p, &last, &limit};
+    return cudaLaunchCooperativeKernel((const void *)pico::dyn::maint::maint_kernel,
+                                       dim3(cfg.sms * per_sm), dim3(pico::kThreads), args, 0, s) ==
+           cudaSuccess;
+}
+
+}  // namespace
+
 pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
                           int64_t capacity_arcs, pico_stream_t stream)
 {
@@ -776,6 +1000,7 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
                  cudaSuccess;
     }
     ok = ok && cudaMalloc(&d->core, (size_t)n * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&d->cd, (size_t)n * sizeof(int)) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(d->rp[0], row_ptr, (size_t)(n + 1) * sizeof(long long),
                                cudaMemcpyDeviceToDevice, s) == cudaSuccess;
     ok = ok && (m == 0 || cudaMemcpyAsync(d->ci[0], col_idx, (size_t)m * sizeof(int),
@@ -783,12 +1008,18 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
     ok = ok && pico_coreness_i64(reinterpret_cast<const int64_t *>(d->rp[0]), d->ci[0], n, m,
                                  d->core, PICO_ALGO_AUTO, stream) ==
                    PICO_OK;
+    // cd for the first insertion batch: one count over all arcs
+    void *ws = nullptr;
+    ok = ok && cudaMallocAsync(&ws, pico::dyn::maint_ws_bytes(n, m), s) == cudaSuccess;
+    ok = ok && launch_maint(d, d->rp[0], d->ci[0], m, nullptr, 0, false, true, ws, s, cfg, last);
+    if (ws) cudaFreeAsync(ws, s);
     ok = ok && sync_status(s) == PICO_OK && pico_last_device_status(stream) == PICO_OK;
     if (!ok) {
         cudaGetLastError();
         pico_dyn_destroy(d);
         return nullptr;
     }
+    d->cd_valid = true;
     return d;
 }
 
@@ -895,6 +1126,8 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     // the graph is consistent: switch to it and bring the coreness up to date
     d->cur = 1 - d->cur;
     d->m = m_new;
+    const bool cd_was_valid = d->cd_valid;
+    d->cd_valid = false;   // until insertion passes leave it exact
     if (n_del > 0 && m_new > 0) {
         rc = pico::launch_histocore<long long>(nrp, nci, n, m_new, d->core, ws2, last, s, cfg,
                                                d->core);
@@ -902,54 +1135,18 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     } else if (n_del > 0) {
         ok = cudaMemsetAsync(d->core, 0, (size_t)n * sizeof(int), s) == cudaSuccess;
     }
-    if (ok && n_ins > 0) {
-        pico::dyn::maint::Params p{};
-        Carver cw(ws2);
-        p.rp = nrp;
-        p.ci = nci;
-        p.n = n;
-        p.m = m_new;
-        p.core = d->core;
-        p.ctl = cw.take<pico::Ctrl>(1);
-        p.cd = cw.take<int>(n);
-        p.sup = cw.take<int>(n);
-        p.flag = cw.take<unsigned char>(n);
-        p.cs = cw.take<int>(n);
-        p.qs = cw.take<int>(n);
-        p.rs = cw.take<int>(n);
-        p.cap = (unsigned)pico::chunk_capacity(m_new);
-        p.allb = cw.take<int2>(p.cap);
-        p.cb = cw.take<int2>(p.cap);
-        p.qb = cw.take<int2>(p.cap);
-        p.rb = cw.take<int2>(p.cap);
-        p.tn = cfg.tn;
-        p.max_passes = (int)std::min<long long>(n_ins + 1, 1ll << 30);
-        ok = cudaMemsetAsync(p.ctl, 0, sizeof(pico::Ctrl), s) == cudaSuccess;
-        if (ok) {
-            static int occ[64] = {};
-            int &o = occ[cfg.device & 63];
-            if (o == 0 &&
-                (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pico::dyn::maint::maint_kernel,
-                                                               pico::kThreads, 0) != cudaSuccess ||
-                 o <= 0))
-                ok = false;
-            if (ok) {
-                const int per_sm = o < cfg.max_blocks_per_sm ? o : cfg.max_blocks_per_sm;
-                unsigned long long limit = cfg.limit_ns;
-                void *args[] = {&p, &last, &limit};
-                ok = cudaLaunchCooperativeKernel((const void *)pico::dyn::maint::maint_kernel,
-                                                 dim3(cfg.sms * per_sm), dim3(pico::kThreads), args,
-                                                 0, s) == cudaSuccess;
-            }
-        }
-    }
+    if (ok && n_ins > 0)
+        ok = launch_maint(d, nrp, nci, m_new, ins, n_ins, cd_was_valid && n_del == 0, false, ws2,
+                          s, cfg, last);
     cudaFreeAsync(ws, s);
     if (!ok) {
         cudaGetLastError();
         return PICO_ERR_CUDA;
     }
     if (sync_status(s) != PICO_OK) return PICO_ERR_CUDA;
-    return pico_last_device_status(stream);
+    const int st = pico_last_device_status(stream);
+    d->cd_valid = st == PICO_OK && n_ins > 0;
+    return st;
 }
 
 int pico_dyn_coreness(pico_dyn *d, int32_t *out_core, pico_stream_t stream)
@@ -996,6 +1193,7 @@ void pico_dyn_destroy(pico_dyn *d)
         if (d->ci[i]) cudaFree(d->ci[i]);
     }
     if (d->core) cudaFree(d->core);
+    if (d->cd) cudaFree(d->cd);
     cudaGetLastError();
     delete d;
 }

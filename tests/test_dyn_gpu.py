@@ -142,3 +142,66 @@ def test_bad_batches_leave_the_state_unchanged(pico):
     assert e.value.status == pico.PICO_ERR_INVALID_ARG
     small.update(insert=[(0, 2), (0, 4)])     # 24 arcs fit
     check(pico, small, 10, edges_of(g) | {(0, 2), (0, 4)})
+
+
+@pytest.mark.parametrize("L", [100, 600])
+def test_ladder_closes_into_a_prism(pico, L):
+    # A 2 x L ladder has coreness 2 (its four corners have degree 2). Closing
+    # both rails makes the prism C_L x K2, which is 3-regular: every vertex
+    # rises to 3. The region of the first pass spreads from the four endpoints
+    # along the rails, about L / 2 levels: within the search's level bound for
+    # L = 100, beyond it (every candidate taken instead) for L = 600.
+    edges = set()
+    for i in range(L):
+        edges.add((i, L + i))
+        if i + 1 < L:
+            edges.add((i, i + 1))
+            edges.add((L + i, L + i + 1))
+    n = 2 * L
+    g = gg.from_edge_list(sorted(edges), n)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=2 * len(edges) + 8)
+    assert (dg.coreness().cpu() == 2).all()
+    ins = [(0, L - 1), (L, 2 * L - 1)]
+    dg.update(insert=ins)
+    assert (dg.coreness().cpu() == 3).all()
+    check(pico, dg, n, edges | set(ins))
+    st = pico.pico_get_stats()
+    assert st["algo"] == pico.PICO_STATS_MAINTENANCE and st["frontier"] == n
+
+
+def test_insertions_far_from_other_candidates_stay_local(pico):
+    # A 2 x 50 ladder (96 vertices of degree 3 at coreness 2: all candidates
+    # to rise) and, apart from it, a path of 10 vertices closed into a cycle by
+    # the batch. Only the path's vertices are connected to the inserted edge,
+    # so the passes' regions hold at most those 10, and the ladder stays at 2.
+    L = 50
+    edges = {(i, L + i) for i in range(L)}
+    edges |= {(i, i + 1) for i in range(L - 1)} | {(L + i, L + i + 1) for i in range(L - 1)}
+    n = 2 * L + 10
+    edges |= {(2 * L + i, 2 * L + i + 1) for i in range(9)}
+    g = gg.from_edge_list(sorted(edges), n)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=2 * len(edges) + 8)
+    ins = [(2 * L, 2 * L + 9)]
+    dg.update(insert=ins)
+    check(pico, dg, n, edges | set(ins))
+    assert dg.coreness().cpu().tolist() == [2] * n
+    st = pico.pico_get_stats()
+    assert st["algo"] == pico.PICO_STATS_MAINTENANCE and st["frontier"] == 10
+    assert st["active"] <= 10, st["active"]
+
+
+def test_consecutive_insertion_batches(pico):
+    # Pure insertion batches reuse the neighbour counts the previous passes
+    # left (counted once at creation, then kept exact); a deletion batch
+    # invalidates them and the next insertion batch counts them again.
+    rng = np.random.default_rng(74)
+    g = gg.rmat_graph(13, 8, 75)
+    n = g.n
+    edges = edges_of(g)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=2 * g.arcs)
+    for k_ins, k_del in [(300, 0), (1, 0), (800, 0), (0, 400), (300, 0), (200, 0), (100, 100),
+                         (400, 0)]:
+        ins, dele = random_batch(rng, n, edges, k_ins, k_del)
+        dg.update(insert=ins, delete=dele)
+        edges = (edges - set(dele)) | set(ins)
+        check(pico, dg, n, edges)
