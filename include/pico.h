@@ -350,7 +350,7 @@ void pico_dyn_destroy(pico_dyn *d);
  * and give the same results and rounds; pulling scans more arcs but edits
  * one row at a time, which keeps the edits in L2 when the rows a round
  * touches exceed it. mode: PICO_UPDATE_*; pull_pct: 1..100, the auto-mode
- * threshold (default 40). Returns PICO_ERR_INVALID_ARG for other values.
+ * threshold (default 50). Returns PICO_ERR_INVALID_ARG for other values.
  */
 int pico_set_histo_update(int mode, int pull_pct);
 int pico_get_histo_update(int *mode, int *pull_pct);

@@ -370,7 +370,7 @@ class DynamicGraph:
             pass
 
 
-PULL_PCT_DEFAULT = 40
+PULL_PCT_DEFAULT = 50
 
 
 def pico_set_histo_update(mode: int, pull_pct: int = PULL_PCT_DEFAULT) -> int:

@@ -36,7 +36,7 @@ constexpr int kMinChunk = 64, kMaxChunk = 4096;
 // formulation of Alg. 6), pull into every vertex whose row an edit can reach,
 // or choose per round (auto).
 constexpr int kUpdateAuto = 0, kUpdatePush = 1, kUpdatePull = 2;
-constexpr int kPullPct = 40;                  // auto: pull when the changed vertices
+constexpr int kPullPct = 50;                  // auto: pull when the changed vertices
                                               // hold >= this % of the arcs ...
 constexpr long long kPullMinArcs = 1ll << 22;  // ... of a graph with at least this many
 
