@@ -194,6 +194,33 @@ def test_histocore_update_directions(pico, update_mode, mode, name, make):
         assert st["pull_rounds"] == 0 and st["pulled"] == 0
 
 
+@pytest.mark.parametrize("mode", ["push", "pull"])
+def test_histocore_wide_estimates(pico, update_mode, mode):
+    """Hubs of degree above 65,534: their {old, new} records do not fit the
+    packed 16-bit form that pull rounds gather, so readers fall back to the
+    full record. Two hubs (70,000 and 66,000 leaves, triangles through the
+    first) each touch 10 members of a K_30, whose rows their drop edits."""
+    edges = [(0, i) for i in range(1, 70001)]
+    edges += [(1 + 2 * i, 2 + 2 * i) for i in range(500)]          # triangles with hub 0
+    hub1 = 70001
+    edges += [(hub1, i) for i in range(70002, 70002 + 66000)]
+    base = 70002 + 66000
+    edges += [(base + a, base + b) for a in range(30) for b in range(a + 1, 30)]
+    edges += [(0, base + a) for a in range(10)] + [(hub1, base + 10 + a) for a in range(10)]
+    n = base + 30
+    g = gg.from_edge_list(edges, n)
+    rp, ci = g.numpy()
+    update_mode(mode)
+    got, st = run(pico, g, "histocore")
+    assert_same(got, oracle.bz_coreness(rp, ci), f"wide estimates {mode}")
+    _, ost = oracle.histocore(rp, ci)
+    assert ost["updates"] > 0
+    assert st["rounds"] == ost["rounds"] and st["frontier"] == ost["frontier"]
+    assert st["atomics"] == g.arcs + 2 * ost["updates"]
+    if mode == "pull":
+        assert st["pull_rounds"] == st["rounds"]
+
+
 def test_histocore_auto_pulls_large_rounds(pico, update_mode):
     """R-MAT scale 18 (8.4 M arcs): the auto mode pulls the first rounds,
     whose changed vertices hold most arcs, and pushes the later ones."""
