@@ -411,8 +411,9 @@ __device__ __forceinline__ void sum_done(const Params<Off> &p, int par, unsigned
 }
 
 // Slots each thread reads per step of a warp or CTA walk (consecutive,
-// descending): a CTA step covers 4 x 512 slots, a warp step 4 x 32.
+// descending): a warp step covers 4 x 32 slots, a CTA step 8 x 512.
 constexpr int kWalkSlots = 4;
+constexpr int kBlockWalkSlots = 8;
 
 // SumHisto by one CTA for a vertex with a large estimate.
 template <typename Off>
@@ -424,11 +425,11 @@ __device__ void sum_block(const Params<Off> &p, int par, unsigned *live, int v, 
     const int K = (int)rec.x;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int carry = 0;
-    for (int top = K; top >= 1; top -= kWalkSlots * (int)blockDim.x) {
-        const int s0 = top - kWalkSlots * (int)threadIdx.x;   // this thread: s0, s0 - 1, ...
-        int r[kWalkSlots], t = 0;
+    for (int top = K; top >= 1; top -= kBlockWalkSlots * (int)blockDim.x) {
+        const int s0 = top - kBlockWalkSlots * (int)threadIdx.x;   // this thread: s0, s0 - 1, ...
+        int r[kBlockWalkSlots], t = 0;
 #pragma unroll
-        for (int j = 0; j < kWalkSlots; ++j) {
+        for (int j = 0; j < kBlockWalkSlots; ++j) {
             const int slot = s0 - j;
             t += slot >= 1 ? ldcg(p.histo + rs + slot - 1) : 0;
             r[j] = t;
@@ -456,9 +457,9 @@ __device__ void sum_block(const Params<Off> &p, int par, unsigned *live, int v, 
         const int before = carry + s[32 + warp] + inc - t;   // slots above s0
         int found = INT_MAX, frun = 0;
 #pragma unroll
-        for (int j = kWalkSlots - 1; j >= 0; --j)
+        for (int j = kBlockWalkSlots - 1; j >= 0; --j)
             if (s0 - j >= 1 && before + r[j] >= s0 - j) {
-                found = kWalkSlots * (int)threadIdx.x + j;
+                found = kBlockWalkSlots * (int)threadIdx.x + j;
                 frun = before + r[j];
             }
         if (found != INT_MAX) atomicMin(&s[64], found);
@@ -466,7 +467,7 @@ __device__ void sum_block(const Params<Off> &p, int par, unsigned *live, int v, 
         const int first = s[64];   // the highest slot that qualifies
         if (first != INT_MAX) {
             if (first == found) {
-                const int slot = s0 - first % kWalkSlots;
+                const int slot = s0 - first % kBlockWalkSlots;
                 slots += (unsigned long long)(K - slot + 1);
                 sum_done(p, par, live, v, rs, K, slot, frun, acc);
             }
