@@ -33,8 +33,9 @@
 // adjacency and, for each neighbour w that changed in this round, applies
 // w's edit to u's row. With a symmetric adjacency both forms apply the same
 // multiset of edits (arc (v, u) pushed is arc (u, v) pulled), so the
-// histograms, the next V_cnt (decided by the same returning decrement of
-// slot K) and the result are identical; only the order of the edits differs,
+// histograms, the next V_cnt (the same set of vertices whose slot K fell
+// below K, see the deferred decision below) and the result are identical;
+// only the order of the edits differs,
 // and a warp pulling 32 consecutive rows edits one contiguous stretch of the
 // histogram. Pulling scans the arcs of every row that an edit can reach
 // instead of those of the changed vertices, so the auto mode pulls only in
