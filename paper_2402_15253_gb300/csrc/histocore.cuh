@@ -389,26 +389,16 @@ __device__ __forceinline__ long long sum_apply(const Params<Off> &p, int par, in
     return d;
 }
 
-// Lists a changed vertex of degree d for UpdateHisto (single-thread path).
+// Lists a changed vertex of small degree d for UpdateHisto; a larger one is
+// listed by its chunks, which the caller's warp or CTA writes together.
 template <typename Off>
-__device__ __forceinline__ void list_changed(const Params<Off> &p, unsigned *live, int v,
-                                             long long d)
+__device__ __forceinline__ void list_small(const Params<Off> &p, unsigned *live, int v,
+                                           long long d)
 {
-    if (d < 0) return;
-    if (d <= p.tn.small_deg) {
-        const unsigned pos = atomicAdd(&live[L_US], 1u);
-        if (pos < (unsigned)p.n) p.us[pos] = v;
-        else set_error(p.ctl, kErrNotConverged);
-    } else if (!push_chunks(v, d, p.ub, &live[L_UB], p.ub_cap, p.tn.chunk)) {
-        set_error(p.ctl, kErrNotConverged);
-    }
-}
-
-template <typename Off>
-__device__ __forceinline__ void sum_done(const Params<Off> &p, int par, unsigned *live, int v,
-                                         Off rs, int K, int h, int sum, RoundAcc &acc)
-{
-    list_changed(p, live, v, sum_apply(p, par, v, rs, K, h, sum, acc));
+    if (d < 0 || d > p.tn.small_deg) return;
+    const unsigned pos = atomicAdd(&live[L_US], 1u);
+    if (pos < (unsigned)p.n) p.us[pos] = v;
+    else set_error(p.ctl, kErrNotConverged);
 }
 
 // Slots each thread reads per step of a warp or CTA walk (consecutive,
@@ -470,8 +460,24 @@ __device__ void sum_block(const Params<Off> &p, int par, unsigned *live, int v, 
             if (first == found) {
                 const int slot = s0 - first % kBlockWalkSlots;
                 slots += (unsigned long long)(K - slot + 1);
-                sum_done(p, par, live, v, rs, K, slot, frun, acc);
+                const long long d = sum_apply(p, par, v, rs, K, slot, frun, acc);
+                list_small(p, live, v, d);
+                unsigned nch = 0, pos = 0;
+                if (d > p.tn.small_deg) {   // the CTA writes the chunk entries
+                    nch = (unsigned)((d + p.tn.chunk - 1) / p.tn.chunk);
+                    pos = atomicAdd(&live[L_UB], nch);
+                    if ((unsigned long long)pos + nch > p.ub_cap) {
+                        set_error(p.ctl, kErrNotConverged);
+                        nch = 0;
+                    }
+                }
+                s[65] = (int)nch;
+                s[66] = (int)pos;
             }
+            __syncthreads();
+            const unsigned nch = (unsigned)s[65], pos = (unsigned)s[66];
+            for (unsigned c = threadIdx.x; c < nch; c += blockDim.x)
+                p.ub[pos + c] = make_int2(v, (int)c);
             __syncthreads();
             return;
         }
@@ -517,11 +523,15 @@ __device__ __forceinline__ void sum_warp(const Params<Off> &p, int par, unsigned
         const unsigned b = __ballot_sync(kFull, found < kWalkSlots);
         if (b) {
             const int L = __ffs(b) - 1;   // the lowest lane holds the highest slots
+            long long d = -1;
             if (lane == L) {
                 const int slot = s0 - found;
                 slots += (unsigned long long)(K - slot + 1);
-                sum_done(p, par, live, v, rs, K, slot, frun, acc);
+                d = sum_apply(p, par, v, rs, K, slot, frun, acc);
+                list_small(p, live, v, d);
             }
+            warp_push_chunks(lane == L && d > p.tn.small_deg, v, d, p.ub, &live[L_UB], p.ub_cap,
+                             p.ctl, p.tn.chunk);
             return;
         }
         carry += __shfl_sync(kFull, inc, 31);
@@ -711,7 +721,8 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
                 if (pos < (unsigned)n) p.us[pos] = v;
                 else set_error(ctl, kErrNotConverged);
             }
-            if (d > p.tn.small_deg) list_changed(p, live, v, d);
+            warp_push_chunks(d > p.tn.small_deg, v, d, p.ub, &live[L_UB], p.ub_cap, ctl,
+                             p.tn.chunk);
         }
         fold_round(acc, live);
         if (!dom.sync()) return;
