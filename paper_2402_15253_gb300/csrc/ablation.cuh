@@ -447,11 +447,9 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
                 __syncwarp();
                 if ((threadIdx.x & 31) == 0) p.cnt[v] = 0;
                 const long long d = (long long)(p.rp[v + 1] - p.rp[v]);
-                if ((threadIdx.x & 31) == 0 && in) {
-                    if (!push_chunks(v, d, p.fb, &live[L_FB], p.cap, p.tn.chunk))
-                        set_error(ctl, kErrNotConverged);
-                    atomicAdd(&live[L_NFRONT], 1u);
-                }
+                if ((threadIdx.x & 31) == 0 && in) atomicAdd(&live[L_NFRONT], 1u);
+                warp_push_chunks((threadIdx.x & 31) == 0 && in, v, d, p.fb, &live[L_FB], p.cap,
+                                 ctl, p.tn.chunk);
             };
             for_vertices(p.as[par], nas, p.ab[par], nab, tid, nthreads, gwarp, nwarps,
                          front_thread, front_warp);
@@ -497,13 +495,13 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
             auto sum_warp = [&](int v) {
                 const int K = ldcg(p.est + v);
                 const int h = hindex_warp(p, v, K);
+                const long long d = (long long)(p.rp[v + 1] - p.rp[v]);
                 if ((threadIdx.x & 31) == 0 && h < K) {
                     p.newv[v] = h;
-                    const long long d = (long long)(p.rp[v + 1] - p.rp[v]);
-                    if (!push_chunks(v, d, p.cb, &live[L_CB], p.cap, p.tn.chunk))
-                        set_error(ctl, kErrNotConverged);
                     atomicAdd(&live[L_NCHG], 1u);
                 }
+                warp_push_chunks((threadIdx.x & 31) == 0 && h < K, v, d, p.cb, &live[L_CB], p.cap,
+                                 ctl, p.tn.chunk);
             };
             for_vertices(fs, nfs, fb, nfb, tid, nthreads, gwarp, nwarps, sum_thread, sum_warp);
         }

@@ -597,10 +597,9 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
         const unsigned nch =
             d > p.tn.small_deg ? (unsigned)((d + p.tn.chunk - 1) / p.tn.chunk) : 0u;
         const unsigned pos = block_alloc(nch, &live[L_ALLB], s_tmp);
-        if (nch && (unsigned long long)pos + nch <= p.cap)
-            for (unsigned c = 0; c < nch; ++c) p.allb[pos + c] = make_int2((int)v, (int)c);
-        else if (nch)
-            set_error(ctl, kErrNotConverged);
+        const bool fits = (unsigned long long)pos + nch <= p.cap;
+        if (nch && !fits) set_error(ctl, kErrNotConverged);
+        warp_fill_chunks(fits ? nch : 0u, pos, (int)v, p.allb);
     }
     if (p.cd_valid) {   // the inserted arcs join the counts
         for (long long i = tid; i < p.n_ins; i += nthreads) {
@@ -746,12 +745,10 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
                                    p.cap, ctl, p.tn);
             },
             [&](int v) {
-                if ((threadIdx.x & 31) == 0 && ldcg(p.sup + v) < ldcg(p.core + v) + 1) {
-                    p.flag[v] = 3;
-                    if (!push_chunks(v, p.rp[v + 1] - p.rp[v], p.qb, &live[L_QB], p.cap,
-                                     p.tn.chunk))
-                        set_error(ctl, kErrNotConverged);
-                }
+                const bool out = ldcg(p.sup + v) < ldcg(p.core + v) + 1;   // the same in every lane
+                if ((threadIdx.x & 31) == 0 && out) p.flag[v] = 3;
+                warp_push_chunks((threadIdx.x & 31) == 0 && out, v, p.rp[v + 1] - p.rp[v], p.qb,
+                                 &live[L_QB], p.cap, ctl, p.tn.chunk);
             });
         if (!dom.sync()) return;
         if (threadIdx.x == 0) ++st[kStBarriers];
@@ -801,19 +798,19 @@ __device__ void run(const Params &p, GridDom &dom, unsigned *s_tmp, unsigned lon
                 if ((threadIdx.x & 31) == 0 && c) atomicAdd(&live[L_RAISED], c);
             },
             [&](int v) {
+                bool up = false;
                 if ((threadIdx.x & 31) == 0) {
-                    const bool up = __ldcg(p.flag + v) == 1;
+                    up = __ldcg(p.flag + v) == 1;
                     if (up) {
                         p.core[v] = ldcg(p.core + v) + 1;
                         p.cd[v] = 0;
                         atomicAdd(&live[L_RAISED], 1u);
-                        if (!push_chunks(v, p.rp[v + 1] - p.rp[v], p.rb, &live[L_RB], p.cap,
-                                         p.tn.chunk))
-                            set_error(ctl, kErrNotConverged);
                     }
                     p.flag[v] = up ? 4 : 0;
                     p.reg[v] = 0;
                 }
+                warp_push_chunks(up, v, p.rp[v + 1] - p.rp[v], p.rb, &live[L_RB], p.cap, ctl,
+                                 p.tn.chunk);
             });
         if (!dom.sync()) return;
         if (threadIdx.x == 0) {

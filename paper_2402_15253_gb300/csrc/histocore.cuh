@@ -628,10 +628,9 @@ __device__ void run(const Params<Off> &p0, Dom &dom, unsigned *s_tmp, unsigned l
         const unsigned nch =
             d > p.tn.small_deg ? (unsigned)((d + p.tn.chunk - 1) / p.tn.chunk) : 0u;
         const unsigned pos = block_alloc(nch, &live[L_IB], s_tmp);
-        if (nch && (unsigned long long)pos + nch <= p.ub_cap)
-            for (unsigned c = 0; c < nch; ++c) ilist[pos + c] = make_int2((int)v, (int)c);
-        else if (nch)
-            set_error(ctl, kErrNotConverged);
+        const bool fits = (unsigned long long)pos + nch <= p.ub_cap;
+        if (nch && !fits) set_error(ctl, kErrNotConverged);
+        warp_fill_chunks(fits ? nch : 0u, pos, (int)v, ilist);
     }
     if (!dom.sync()) return;
     if (threadIdx.x == 0) ++st[kStBarriers];

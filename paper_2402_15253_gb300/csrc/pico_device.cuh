@@ -358,15 +358,23 @@ __device__ __forceinline__ void block_min_to(int v, int *target, int *s)
 // ---------------------------------------------------------------------------
 // load-balanced adjacency expansion
 // ---------------------------------------------------------------------------
-// Appends the chunk entries of a large vertex (degree d > small_deg).
-__device__ __forceinline__ bool push_chunks(int v, long long d, int2 *list, unsigned *counter,
-                                            unsigned cap, int chunk)
+// Writes reserved chunk entries: every lane with nch > 0 owns entries
+// pos .. pos + nch - 1 of vertex v (reserved by the caller). A lane writes a
+// short list itself; the warp writes the longer ones (hubs) together.
+__device__ __forceinline__ void warp_fill_chunks(unsigned nch, unsigned pos, int v, int2 *list)
 {
-    const unsigned nch = (unsigned)((d + chunk - 1) / chunk);
-    const unsigned pos = atomicAdd(counter, nch);
-    if ((unsigned long long)pos + nch > cap) return false;
-    for (unsigned c = 0; c < nch; ++c) list[pos + c] = make_int2(v, (int)c);
-    return true;
+    constexpr unsigned kOwn = 8;
+    const int lane = threadIdx.x & 31;
+    if (nch <= kOwn)
+        for (unsigned c = 0; c < nch; ++c) list[pos + c] = make_int2(v, (int)c);
+    unsigned m = __ballot_sync(kFull, nch > kOwn);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const unsigned nn = __shfl_sync(kFull, nch, src), pp = __shfl_sync(kFull, pos, src);
+        const int vv = __shfl_sync(kFull, v, src);
+        for (unsigned c = lane; c < nn; c += 32) list[pp + c] = make_int2(vv, (int)c);
+    }
 }
 
 // Warp-cooperative append of the chunk entries of large vertices: every
