@@ -205,3 +205,17 @@ def test_consecutive_insertion_batches(pico):
         dg.update(insert=ins, delete=dele)
         edges = (edges - set(dele)) | set(ins)
         check(pico, dg, n, edges)
+
+
+def test_starting_from_no_edges(pico):
+    # An edgeless graph: the neighbour counts start over zero arcs, then a
+    # triangle and a pendant edge arrive in two insertion batches.
+    n = 6
+    g = gg.from_edge_list([], n)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=32)
+    assert (dg.coreness().cpu() == 0).all()
+    dg.update(insert=[(0, 1), (1, 2)])
+    check(pico, dg, n, {(0, 1), (1, 2)})
+    dg.update(insert=[(0, 2), (2, 3)])
+    check(pico, dg, n, {(0, 1), (1, 2), (0, 2), (2, 3)})
+    assert dg.coreness().cpu().tolist() == [2, 2, 2, 1, 0, 0]
