@@ -613,7 +613,8 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": sample, "step": "one BZ decomposition"},
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "sample": sample,
+                   "step": "one BZ decomposition of the sample"},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
                          "sample": f"{sample}: same recipe at reduced scale, "
                                    f"{edges} undirected edges, single-threaded BZ"},
