@@ -82,14 +82,15 @@ def kernel_source_hash(method: str) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, method: str, arcs: int):
+def recorded_traffic(workload: str, method: str, arcs: int, profiles_dir: str | None = None):
     """DRAM bytes per launch from a committed ncu summary of `method`, if it
     was taken on the current kernel sources (its `kernel_source_hash` line
     matches). A capture of a smaller workload of the same family is scaled to
     this one by the arc count (the traffic of both methods grows with the
     arcs they scan). Returns (bytes or None, source description)."""
     best = None
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{method}_*.md"))):
+    pdir = profiles_dir or os.path.join(ROOT, "profiles")
+    for path in sorted(glob.glob(os.path.join(pdir, f"{method}_*.md"))):
         text = open(path).read()
         m_hash = re.search(r"kernel_source_hash\s*=\s*`?([0-9a-f]+)", text)
         m_bytes = re.search(r"dram_bytes_per_launch\s*=\s*`?([0-9.eE+]+)", text)
