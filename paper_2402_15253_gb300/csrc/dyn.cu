@@ -16,18 +16,23 @@
 //      With insertions in the batch the start is not an upper bound, but the
 //      result is still a lower bound of the new coreness.
 //   3. Insertions: coreness can only rise; the value after step 2 is a lower
-//      bound. A pass tries to raise every vertex by one: the candidates are
-//      the vertices w with at least core(w) + 1 neighbours of core >= core(w);
-//      each counts its support (neighbours of higher core, or of equal core
-//      that are candidates) and candidates whose support falls below
-//      core(w) + 1 are peeled, which lowers their equal-core candidate
-//      neighbours' support, wave by wave as in PeelOne's dynamic frontier.
-//      The survivors of level K together with the vertices of core > K have
-//      minimum degree K + 1, so they lie in the (K + 1)-core and rise by one.
-//      Passes repeat until one raises nothing. Then no vertex is below its
-//      coreness: for the smallest k with a vertex below k in the true
-//      k-core X, those vertices all have core k - 1, are candidates, and keep
-//      a support of at least k from X through every peel, so they would rise.
+//      bound. A pass tries to raise vertices by one: the candidates are the
+//      vertices w with at least core(w) + 1 neighbours of core >= core(w)
+//      (that count, cd, is kept between batches); the pass works on its
+//      region, the candidates connected to a seed through candidates of equal
+//      core (seeds: the inserted edges' endpoints, then the vertices the
+//      previous pass raised and their neighbours; see run() for why no other
+//      vertex can rise). Each region vertex counts its support (neighbours of
+//      higher core, or of equal core that are candidates) and those whose
+//      support falls below core(w) + 1 are peeled, which lowers their
+//      equal-core candidate neighbours' support, wave by wave as in PeelOne's
+//      dynamic frontier. The survivors of level K together with the vertices
+//      of core > K have minimum degree K + 1, so they lie in the (K + 1)-core
+//      and rise by one. Passes repeat until one raises nothing. Then no vertex
+//      is below its coreness: for the smallest k with a vertex below k in the
+//      true k-core X, those vertices all have core k - 1, are candidates, and
+//      keep a support of at least k from X through every peel, so they rise
+//      once their component is in a region, which it is.
 #include <algorithm>
 #include <cstring>
 
