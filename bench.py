@@ -160,19 +160,32 @@ class ClockSampler:
 
 
 def cpu_oracle_time(sample: str, repeats: int = 1):
-    """Single-threaded Batagelj-Zaversnik on a host copy of `sample`."""
+    """Single-threaded Batagelj-Zaversnik on a host copy of `sample`, and the
+    parallel CPU peel (cpu_peel, all host cores) on the same copy, checked
+    against it. Returns (edges, oracle s, parallel s, parallel threads)."""
+    import numpy as np
     import oracle
+    import cpu_peel
     g = make_graph(sample, "cuda")
     rp, ci = g.numpy()
     del g
-    oracle.lib()   # load the library outside the timing
+    oracle.lib()   # load the libraries outside the timing
+    cpu_peel.lib()
     times = []
     for _ in range(repeats):
         t0 = time.perf_counter()
-        oracle.bz_coreness(rp, ci)
+        want = oracle.bz_coreness(rp, ci)
         times.append(time.perf_counter() - t0)
+    cpu_peel.coreness(rp, ci)   # warm-up (thread pool, pages)
+    ptimes = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        got = cpu_peel.coreness(rp, ci)
+        ptimes.append(time.perf_counter() - t0)
+    if not np.array_equal(got, want):
+        raise AssertionError("the parallel CPU peel disagrees with the oracle")
     edges = int(rp[-1]) // 2
-    return edges, statistics.median(times)
+    return edges, statistics.median(times), statistics.median(ptimes), cpu_peel.threads()
 
 
 def bench_batched(pico, dev, stream, G: int, reps: int = 5):
@@ -862,12 +875,17 @@ def main():
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sample = CPU_SAMPLE.get(args.workload, args.workload)
-        edges, secs = cpu_oracle_time(sample)
+        edges, secs, psecs, threads = cpu_oracle_time(sample)
         line["cpu_baseline"] = {"value": edges / secs, "unit": "edges/s", "cores": 1,
                                 "kind": "oracle",
                                 "sample": f"{sample}: same recipe at reduced scale, {edges} "
                                           f"undirected edges, one single-threaded "
                                           f"Batagelj-Zaversnik run ({secs:.1f} s)"}
+        line["cpu_parallel"] = {"value": edges / psecs, "unit": "edges/s", "cores": threads,
+                                "kind": "OpenMP level-synchronous peel (a comparison, not the "
+                                        "oracle; its result is checked against the oracle)",
+                                "sample": f"{sample}: the same graph, median of 3 runs "
+                                          f"({psecs:.2f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
