@@ -263,7 +263,9 @@ __global__ void segments_kernel(const unsigned char *touched, long long n, const
 
 // The arcs of the untouched rows keep their order and move by the shift of
 // the touched row before them (0 before the first): one coalesced pass over
-// the old arcs, 1024 per warp, with a binary search once per warp.
+// the old arcs. Each warp copies one contiguous range, 1024 arcs per step: one
+// binary search finds the touched row before the range, later steps advance
+// from it, and a step that holds no touched arc copies with a single shift.
 __global__ void __launch_bounds__(512) bulk_copy_kernel(const int *ci, long long m_old,
                                                         int *new_ci, const long long *seg_start,
                                                         const long long *seg_end,
@@ -273,23 +275,36 @@ __global__ void __launch_bounds__(512) bulk_copy_kernel(const int *ci, long long
     const long long nT = *ntp;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long c0 = gw * 1024; c0 < m_old; c0 += nwarps * 1024) {
-        long long i = -1;   // last touched row starting at or before c0
-        if (lane == 0) {
-            long long lo = 0, hi = nT;   // first index with seg_start > c0
-            while (lo < hi) {
-                const long long mid = (lo + hi) >> 1;
-                if (seg_start[mid] <= c0) lo = mid + 1;
-                else hi = mid;
-            }
-            i = lo - 1;
+    const long long span = ((m_old + nwarps - 1) / nwarps + 31) & ~31ll;
+    const long long a0 = gw * span, a1 = a0 + span < m_old ? a0 + span : m_old;
+    if (a0 >= a1) return;
+    long long i = -1;   // last touched row starting at or before the step's first arc
+    if (lane == 0) {
+        long long lo = 0, hi = nT;   // first index with seg_start > a0
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (seg_start[mid] <= a0) lo = mid + 1;
+            else hi = mid;
         }
-        i = __shfl_sync(kFull, i, 0);
-        const long long c1 = c0 + 1024 < m_old ? c0 + 1024 : m_old;
+        i = lo - 1;
+    }
+    i = __shfl_sync(kFull, i, 0);
+    for (long long c0 = a0; c0 < a1; c0 += 1024) {
+        const long long c1 = c0 + 1024 < a1 ? c0 + 1024 : a1;
+        while (i + 1 < nT && seg_start[i + 1] <= c0) ++i;   // the same in every lane
+        const long long se = i >= 0 ? seg_end[i] : -1;
+        const long long ns = i + 1 < nT ? seg_start[i + 1] : LLONG_MAX;
+        if (c0 >= se && c1 <= ns) {   // no touched arc in the step
+            const long long sh = i >= 0 ? shift[i] : 0;
+#pragma unroll 4
+            for (long long e = c0 + lane; e < c1; e += 32) new_ci[e + sh] = ci[e];
+            continue;
+        }
+        long long t = i;
         for (long long e = c0 + lane; e < c1; e += 32) {
-            while (i + 1 < nT && seg_start[i + 1] <= e) ++i;
-            if (i >= 0 && e < seg_end[i]) continue;   // a touched row: copied elsewhere
-            new_ci[e + (i >= 0 ? shift[i] : 0)] = ci[e];
+            while (t + 1 < nT && seg_start[t + 1] <= e) ++t;
+            if (t >= 0 && e < seg_end[t]) continue;   // a touched row: copied elsewhere
+            new_ci[e + (t >= 0 ? shift[t] : 0)] = ci[e];
         }
     }
 }
