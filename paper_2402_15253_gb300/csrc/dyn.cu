@@ -197,9 +197,24 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(long long *a, long long 
     }
 }
 
+// set_has for a table that no thread writes during the kernel (built by an
+// earlier launch): the probes may go through the read-only cache.
+__device__ __forceinline__ bool set_has_ro(const unsigned long long *tab, unsigned mask,
+                                           unsigned long long k)
+{
+    unsigned s = hash_slot(k, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe, s = (s + 1) & mask) {
+        const unsigned long long x = __ldg(tab + s);
+        if (x == k) return true;
+        if (x == 0ull) return false;
+    }
+    return false;
+}
+
 // Copies one old row's surviving arcs: every lane of the warp calls with the
-// same u; arcs [e0, e1) of the old row. Positions come from the row's cursor,
-// one atomic per warp step.
+// same u; arcs [e0, e1) of the old row. 1024 arcs at a time: the lanes first
+// decide which arcs survive (one bit per step), then reserve the survivors'
+// positions with one atomic on the row's cursor, then write them in order.
 __device__ __forceinline__ void copy_piece(int u, long long e0, long long e1, const int *ci,
                                            const long long *new_rp, int *new_ci, int *cursor,
                                            unsigned char tflag, const unsigned long long *instab,
@@ -207,24 +222,40 @@ __device__ __forceinline__ void copy_piece(int u, long long e0, long long e1, co
                                            unsigned delmask, int *err)
 {
     const unsigned lane = threadIdx.x & 31;
-    for (long long e = e0; e < e1; e += 32) {
-        const long long i = e + lane;
-        int v = -1;
-        bool keep = false;
-        if (i < e1) {
-            v = ci[i];
-            keep = true;
-            if ((tflag & 2) && set_has(deltab, delmask, arc_key(u, v))) keep = false;
-            if ((tflag & 1) && set_has(instab, insmask, arc_key(u, v))) fail(err, kExistingArc);
+    const long long r0 = new_rp[u], r1 = new_rp[u + 1];
+    for (long long s0 = e0; s0 < e1; s0 += 1024) {
+        const long long s1 = s0 + 1024 < e1 ? s0 + 1024 : e1;
+        unsigned keepbits = 0;
+        int cnt = 0;
+#pragma unroll 4
+        for (int st = 0; st < 32; ++st) {
+            const long long i = s0 + 32 * st + lane;
+            if (i < s1) {
+                const int v = ci[i];
+                bool keep = true;
+                if ((tflag & 2) && set_has_ro(deltab, delmask, arc_key(u, v))) keep = false;
+                if ((tflag & 1) && set_has_ro(instab, insmask, arc_key(u, v)))
+                    fail(err, kExistingArc);
+                if (keep) {
+                    keepbits |= 1u << st;
+                    ++cnt;
+                }
+            }
         }
-        const unsigned b = __ballot_sync(kFull, keep);
+        const int tot = __reduce_add_sync(kFull, cnt);
         int base = 0;
-        if (lane == 0 && b) base = atomicAdd(cursor + u, __popc(b));
+        if (lane == 0 && tot) base = atomicAdd(cursor + u, tot);
         base = __shfl_sync(kFull, base, 0);
-        if (keep) {
-            const long long pos = new_rp[u] + base + __popc(b & ((1u << lane) - 1u));
-            if (pos < new_rp[u + 1]) new_ci[pos] = v;
-            else fail(err, kMissingArc);
+        int off = 0;
+        for (int st = 0; st < 32; ++st) {
+            const bool keep = (keepbits >> st) & 1u;
+            const unsigned b = __ballot_sync(kFull, keep);
+            if (keep) {
+                const long long pos = r0 + base + off + __popc(b & ((1u << lane) - 1u));
+                if (pos < r1) new_ci[pos] = ci[s0 + 32 * st + lane];
+                else fail(err, kMissingArc);
+            }
+            off += __popc(b);
         }
     }
 }
