@@ -40,10 +40,11 @@ WORKLOADS = {
     "grid4096": "4096 x 4096 4-neighbour grid",
 }
 # bounded CPU samples of each workload for the oracle timing (same recipe, smaller)
-CPU_SAMPLE = {"rmat24": "rmat22", "rmat22": "rmat20", "rmat16": "rmat16",
-              "chunglu24": "rmat22", "grid4096": "grid2048"}
-REF_SAMPLE = {"rmat24": "rmat20", "rmat22": "rmat19", "rmat16": "rmat16",
-              "chunglu24": "rmat20", "grid4096": "grid1024"}
+# (the workload itself where one oracle run takes a few seconds)
+CPU_SAMPLE = {"rmat24": "rmat24", "rmat22": "rmat22", "rmat16": "rmat16",
+              "chunglu24": "chunglu24", "grid4096": "grid4096"}
+REF_SAMPLE = {"rmat24": "rmat24", "rmat22": "rmat22", "rmat16": "rmat16",
+              "chunglu24": "chunglu24", "grid4096": "grid4096"}
 
 
 def make_graph(name, device):
@@ -159,16 +160,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_time(sample: str, repeats: int = 1):
-    """Single-threaded Batagelj-Zaversnik on a host copy of `sample`, and the
-    parallel CPU peel (cpu_peel, all host cores) on the same copy, checked
+def cpu_oracle_time(sample: str, repeats: int = 1, host_csr=None):
+    """Single-threaded Batagelj-Zaversnik on a host copy of `sample` (or on
+    `host_csr`, a (row_ptr, col_idx) pair of numpy arrays of that graph), and
+    the parallel CPU peel (cpu_peel, all host cores) on the same copy, checked
     against it. Returns (edges, oracle s, parallel s, parallel threads)."""
     import numpy as np
     import oracle
     import cpu_peel
-    g = make_graph(sample, "cuda")
-    rp, ci = g.numpy()
-    del g
+    if host_csr is not None:
+        rp, ci = host_csr
+    else:
+        g = make_graph(sample, "cuda")
+        rp, ci = g.numpy()
+        del g
     oracle.lib()   # load the libraries outside the timing
     cpu_peel.lib()
     times = []
@@ -378,12 +383,24 @@ def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int
         rate = f * capacity
         res["loads"][str(f)] = {"offered_graphs_per_s": rate, "served": run(rate, False),
                                 "sequential_plain": run(rate, True)}
-    # the shared per-graph result buffers must hold the oracle's coreness
-    for j in (0, 1, pool_size - 1):
+    # the result buffer of every requested pool graph (written by the last
+    # request for that graph) must hold the oracle's coreness; checked after
+    # the timed runs
+    from concurrent.futures import ThreadPoolExecutor
+    oracle.lib()
+
+    def check(j):
         n, m, rp, ci, out = pool[j]
         want = oracle.bz_coreness(rp.numpy().astype("int64"), ci.numpy()[:m])
-        if not (out[:n].numpy() == want).all():
-            raise AssertionError(f"served result of pool graph {j} differs from the oracle")
+        return bool((out[:n].numpy() == want).all())
+
+    asked = sorted(set(pick))
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        ok = list(ex.map(check, asked))
+    if not all(ok):
+        raise AssertionError(f"served results of pool graphs {[j for j, o in zip(asked, ok) if not o]} "
+                             "differ from the oracle")
+    res["oracle_checked_graphs"] = len(asked)
     return res
 
 
@@ -483,6 +500,62 @@ def bench_auto(pico, rp, ci, n, arcs, ref, stream, reps=3):
     chose = pico.pico_get_stats(stream)["algo"]
     return {"ms": statistics.median(times),
             "method": {v: k for k, v in pico.ALGOS.items()}[chose]}
+
+
+def bench_configs(pico, dev, stream, names=("rmat16", "rmat22", "chunglu24", "grid4096"),
+                  reps: int = 3):
+    """Both methods on each of the other single-graph workloads: the
+    degree-class tuning is autotuned per graph and method first, then each
+    method is timed `reps` times (CUDA events on the launching stream, an L2
+    flush before each run, the median kept). The two methods must agree."""
+    import torch
+    from paper_2402_15253_gb300 import autotune
+    peak, peak_kind = peaks()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    for name in names:
+        g = make_graph(name, dev)
+        rp, ci, n, arcs = g.row_ptr, g.col_idx, g.n, g.arcs
+        w_r = rp.element_size()
+        fn = pico.pico_coreness if w_r == 4 else pico.pico_coreness_i64
+        b_min = w_r * (n + 1) + 8 * arcs + 4 * n
+        outs, rec = {}, {"workload": WORKLOADS[name], "n": n, "arcs": arcs,
+                         "undirected_edges": arcs // 2}
+        for a in ("peelone", "histocore"):
+            best, _ = autotune.tune_single(pico, rp, ci, a, reps=2, use_cache=False)
+            out = torch.empty(n, dtype=torch.int32, device=dev)
+            times = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rc = fn(rp, ci, n, arcs, out, pico.ALGOS[a], stream)
+                e1.record(stream)
+                if rc != 0:
+                    raise pico.PicoError(rc, f"{name} {a}")
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            st = pico.pico_last_device_status(stream)
+            if st != 0:
+                raise pico.PicoError(st, f"{name} {a}")
+            stats = pico.pico_get_stats(stream)
+            ms = statistics.median(times)
+            b_alg = method_bytes(a, stats, n, arcs, w_r)
+            rec[a] = {"ms": ms, "edges_per_s": arcs / 2 / (ms / 1e3),
+                      "alg_frac_of_" + peak_kind: b_alg / (ms / 1e3) / 1e9 / peak,
+                      "bmin_frac_of_" + peak_kind: b_min / (ms / 1e3) / 1e9 / peak,
+                      "tuning": {"small_deg": best[0], "chunk": best[1]},
+                      "stats": {k: stats[k] for k in ("levels", "kmax", "subrounds", "rounds",
+                                                      "pull_rounds", "barriers") if stats[k]}}
+            outs[a] = out
+        if not torch.equal(outs["peelone"], outs["histocore"]):
+            raise AssertionError(f"{name}: PeelOne and HistoCore disagree")
+        rec["kmax"] = int(outs["peelone"].max().item())
+        rec["better"] = min(("peelone", "histocore"), key=lambda a: rec[a]["ms"])
+        res[name] = rec
+        del g, outs
+        torch.cuda.empty_cache()
+    return res
 
 
 def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6,
@@ -607,10 +680,9 @@ def reference_arm(args):
     if rank != 0:
         return 0
     sample = REF_SAMPLE.get(args.workload, "rmat20")
-    import torch  # noqa: F401  (graph generation runs through torch on the CPU here)
-    import graphgen as gg  # noqa: F401
     import oracle
-    g = make_graph(sample, "cpu")
+    import torch
+    g = make_graph(sample, "cuda" if torch.cuda.is_available() else "cpu")   # not timed
     rp, ci = g.numpy()
     del g
     oracle.lib()
@@ -628,10 +700,12 @@ def reference_arm(args):
         "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "sample": sample,
+                   "same_config": sample == args.workload,
                    "step": "one BZ decomposition of the sample"},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample}: same recipe at reduced scale, "
-                                   f"{edges} undirected edges, single-threaded BZ"},
+                         "sample": (f"{sample}: the workload graph itself" if sample == args.workload
+                                    else f"{sample}: same recipe at reduced scale") +
+                                   f", {edges} undirected edges, single-threaded BZ"},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -658,8 +732,10 @@ def main():
                     help="'auto' (autotune each method on the graph) or S,C,T,K: small_deg, "
                          "chunk, batched CTA threads, cluster log2 arcs, for both methods "
                          "(or PeelOne's/HistoCore's, separated by '/')")
-    ap.add_argument("--serve-requests", type=int, default=0,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the served-form measurement (0: skip)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-workload record of the other single-graph workloads")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -769,6 +845,8 @@ def main():
     dom = max(mean_ms, key=mean_ms.get)
     achieved = b_alg[dom] / (mean_ms[dom] / 1000.0) / 1e9
     traffic, traffic_src = recorded_traffic(args.workload, dom, arcs)
+    best = min(mean_ms, key=mean_ms.get)   # the faster method
+    best_traffic, best_traffic_src = recorded_traffic(args.workload, best, arcs)
     methods = {a: {"ms_mean": mean_ms[a], "ms_median": statistics.median(per[a]),
                    "alg_bytes": b_alg[a],
                    "alg_gbs": b_alg[a] / (mean_ms[a] / 1000.0) / 1e9,
@@ -795,8 +873,23 @@ def main():
                      "bytes_per_launch": b_alg[dom], "peak_kind": peak_kind,
                      "bytes_model": BYTES_MODEL[dom],
                      "bmin_bytes": b_min,
-                     "bmin_frac": b_min / (mean_ms[dom] / 1000.0) / 1e9 / peak},
+                     "bmin_frac": b_min / (mean_ms[dom] / 1000.0) / 1e9 / peak,
+                     "traffic_frac": (traffic / (mean_ms[dom] / 1000.0) / 1e9 / peak
+                                      if traffic else None)},
         "tuning": {a: {"small_deg": t[0], "chunk": t[1]} for a, t in tuned.items()},
+        "peelone_edges_per_s": methods["peelone"]["edges_per_s"],
+        "histocore_edges_per_s": methods["histocore"]["edges_per_s"],
+        "roofline_better_method": {
+            "kernel": best, "ms": mean_ms[best], "edges_per_s": m_und / (mean_ms[best] / 1e3),
+            "bound": "hbm", "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+            "achieved": b_alg[best] / (mean_ms[best] / 1e3) / 1e9,
+            "frac": b_alg[best] / (mean_ms[best] / 1e3) / 1e9 / peak,
+            "bytes_per_launch": b_alg[best], "bytes_model": BYTES_MODEL[best],
+            "bmin_achieved": b_min / (mean_ms[best] / 1e3) / 1e9,
+            "bmin_frac": b_min / (mean_ms[best] / 1e3) / 1e9 / peak,
+            "traffic": best_traffic, "traffic_source": best_traffic_src,
+            "traffic_frac": (best_traffic / (mean_ms[best] / 1e3) / 1e9 / peak
+                             if best_traffic else None)},
         "methods": methods,
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
@@ -872,13 +965,25 @@ def main():
         line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)
     if rank == 0 and args.serve_requests > 0:
         line["served"] = bench_serve(pico, dev, args.serve_requests)
+    h_csr = None   # host copy of the workload graph for the CPU baseline
+    if (rank == 0 and ws == 1 and not args.no_cpu_baseline
+            and CPU_SAMPLE.get(args.workload) == args.workload):
+        h_csr = g.numpy()
+    if rank == 0 and not args.no_configs:
+        del g, rp, ci, out
+        torch.cuda.empty_cache()
+        line["configs"] = bench_configs(pico, dev, stream,
+                                        [w for w in ("rmat16", "rmat22", "chunglu24", "grid4096")
+                                         if w != args.workload])
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sample = CPU_SAMPLE.get(args.workload, args.workload)
-        edges, secs, psecs, threads = cpu_oracle_time(sample)
+        edges, secs, psecs, threads = cpu_oracle_time(sample, host_csr=h_csr)
+        what = ("the workload graph itself" if sample == args.workload
+                else "same recipe at reduced scale")
         line["cpu_baseline"] = {"value": edges / secs, "unit": "edges/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": f"{sample}: same recipe at reduced scale, {edges} "
+                                "kind": "oracle", "same_config": sample == args.workload,
+                                "sample": f"{sample}: {what}, {edges} "
                                           f"undirected edges, one single-threaded "
                                           f"Batagelj-Zaversnik run ({secs:.1f} s)"}
         line["cpu_parallel"] = {"value": edges / psecs, "unit": "edges/s", "cores": threads,

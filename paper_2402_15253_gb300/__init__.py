@@ -59,8 +59,9 @@ class PicoError(RuntimeError):
 
 PHASES = ("init", "scan", "wave_tiny", "wave_mid", "wave_wide", "inithisto", "sumhisto",
           "updatehisto")
-# trace-only kinds (counted under "updatehisto" in pico_stats.phase_ns)
-TRACE_KINDS = PHASES + ("updatehisto_pull",)
+# trace-only kinds: a pulled UpdateHisto round (counted under "updatehisto" in
+# pico_stats.phase_ns) and an asynchronous PeelOne level (under "wave_wide")
+TRACE_KINDS = PHASES + ("updatehisto_pull", "level")
 
 
 class pico_stats(ctypes.Structure):
@@ -235,6 +236,7 @@ def pico_coreness_noalloc(row_ptr, col_idx, n: int, m: int, out_core, out_status
 
 PICO_NOALLOC_MAX_VERTICES = 1 << 20
 PICO_NOALLOC_MAX_ARCS = 1 << 24
+
 
 
 def pico_workspace_bytes(n: int, m: int, algo: int) -> int:

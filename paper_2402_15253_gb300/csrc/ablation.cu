@@ -106,7 +106,7 @@ int launch_gpp(const Off *rp, const int *ci, long long n, long long m, int *core
     if (grid <= 0) return -3;
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&p, &last, &limit};
-    if (cudaLaunchCooperativeKernel((const void *)gpp_kernel<Off>, dim3(grid), dim3(kThreads),
+    if (launch_cooperative((const void *)gpp_kernel<Off>, dim3(grid), dim3(kThreads),
                                     args, 0, stream) != cudaSuccess)
         return -3;
     return 0;
@@ -148,7 +148,7 @@ int launch_index2core(const Off *rp, const int *ci, long long n, long long m, in
     if (grid <= 0) return -3;
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&p, &last, &limit};
-    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, stream) !=
+    if (launch_cooperative(fn, dim3(grid), dim3(kThreads), args, 0, stream) !=
         cudaSuccess)
         return -3;
     return 0;

@@ -44,7 +44,9 @@ __device__ __forceinline__ void warp_append_vertex(bool pred, int v, long long d
 
 namespace gpp {
 
-enum : int { L_QS = 0, L_QB = 1, L_RES = 2 };
+// live counters of three consecutive scans (slot = scan index mod 3): a
+// scan resets the next scan's slot, which nobody touches until then
+enum : int { L_QS = 0 /* 0..2 */, L_QB = 3 /* 3..5 */, L_RES = 6 /* 6..8 */ };
 
 template <typename Off>
 struct Params {
@@ -108,11 +110,18 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
 
     int k = 0;
     long long nres = n;
+    unsigned slot = 0;
     const long long max_scans = n + p.rp[n] + 2;   // each scan removes a vertex or raises k
     for (long long scans = 1; nres > 0; ++scans) {
         if (scans > max_scans) {
             if (threadIdx.x == 0) set_error(ctl, kErrNotConverged);
             return;
+        }
+        if (dom.leader()) {
+            const unsigned nx = (slot + 1) % 3;
+            live[L_QS + nx] = 0;
+            live[L_QB + nx] = 0;
+            live[L_RES + nx] = 0;
         }
         // scan every vertex for the frontier {!rem, deg <= k}
         for (long long base = first; base < n; base += nthreads) {
@@ -131,9 +140,9 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
             }
             const bool small = front && d <= p.tn.small_deg;
             unsigned pos, unused;
-            block_push2(small, keep, &live[L_QS], &live[L_RES], pos, unused, s_tmp);
+            block_push2(small, keep, &live[L_QS + slot], &live[L_RES + slot], pos, unused, s_tmp);
             if (small) p.qs[pos] = (int)v;   // at most n frontier vertices in a step
-            warp_push_chunks(front && !small, (int)v, d, p.qb, &live[L_QB], p.qb_cap, ctl,
+            warp_push_chunks(front && !small, (int)v, d, p.qb, &live[L_QB + slot], p.qb_cap, ctl,
                              p.tn.chunk);
         }
         if (!dom.sync()) return;
@@ -141,13 +150,9 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
             ++st[kStBarriers];
             ++st[kStScans];
         }
-        const unsigned nqs = snap[L_QS], nqb = snap[L_QB];
-        nres = (long long)snap[L_RES];
-        if (dom.leader()) {   // nothing appends until the next scan
-            live[L_QS] = 0;
-            live[L_QB] = 0;
-            live[L_RES] = 0;
-        }
+        const unsigned nqs = snap[L_QS + slot], nqb = snap[L_QB + slot];
+        nres = (long long)snap[L_RES + slot];
+        slot = (slot + 1) % 3;
         if (nqs + nqb == 0) {   // no vertex with deg <= k: next k
             ++k;
             continue;

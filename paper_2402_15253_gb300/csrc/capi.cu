@@ -59,6 +59,7 @@ int device_state(DeviceState **out)
         d.cfg.limit_ns = (unsigned long long)env_ll("PICO_WAIT_LIMIT_MS", 4000) * 1000000ull;
         d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk, pico::kClusterLog2};
         d.cfg.batched_threads = pico::kThreads;
+        d.cfg.peel_async = env_ll("PICO_PEEL_WAVES", 0) == 0;
         if (cudaMalloc(&d.last, sizeof(pico::LastResult)) != cudaSuccess) {
             cudaGetLastError();
             return PICO_ERR_OOM;
@@ -105,7 +106,7 @@ size_t single_ws_bytes(long long n, long long m, int algo)
     switch (algo) {
     case PICO_ALGO_PEELONE:
     case PICO_ALGO_PEEL_CAS:
-    case PICO_ALGO_PEEL_ADDBACK: return pico::peelone_ws_bytes(n, m);
+    case PICO_ALGO_PEEL_ADDBACK: return pico::peelone_ws_bytes(n, m, true);
     case PICO_ALGO_HISTOCORE: return pico::histocore_ws_bytes(n, m);
     case PICO_ALGO_GPP: return pico::gpp_ws_bytes(n, m);
     case PICO_ALGO_NBRCORE:

@@ -1019,7 +1019,7 @@ bool launch_maint(pico_dyn *d, const long long *rp, const int *ci, long long m, 
     const int per_sm = o < cfg.max_blocks_per_sm ? o : cfg.max_blocks_per_sm;
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&p, &last, &limit};
-    return cudaLaunchCooperativeKernel((const void *)pico::dyn::maint::maint_kernel,
+    return pico::launch_cooperative((const void *)pico::dyn::maint::maint_kernel,
                                        dim3(cfg.sms * per_sm), dim3(pico::kThreads), args, 0, s) ==
            cudaSuccess;
 }
@@ -1137,7 +1137,7 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
         long long nn = n;
         unsigned long long limit = cfg.limit_ns;
         void *args[] = {&a, &nn, &ctl, &sums, &limit};
-        return cudaLaunchCooperativeKernel((const void *)pico::dyn::scan_kernel, dim3(cfg.sms),
+        return pico::launch_cooperative((const void *)pico::dyn::scan_kernel, dim3(cfg.sms),
                                            dim3(pico::kThreads), args, 0, s) == cudaSuccess;
     };
     bool ok = cudaMemsetAsync(ws, 0, zero_bytes, s) == cudaSuccess;

@@ -102,7 +102,7 @@ int launch_histocore(const Off *rp, const int *ci, long long n, long long m, int
     dim3 grid(cfg.sms * per_sm), block(kThreads);
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&p, &last, &limit};
-    if (cudaLaunchCooperativeKernel((const void *)histocore_kernel<Off>, grid, block, args, 0,
+    if (launch_cooperative((const void *)histocore_kernel<Off>, grid, block, args, 0,
                                     stream) != cudaSuccess)
         return -3;
     return 0;

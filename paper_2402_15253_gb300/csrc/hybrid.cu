@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         use_histo = prefer_histocore(n, hp.m, s_snap[kLiveDmax]);
         if (use_histo)
             histo::run(hp, dom, s_tmp, st, clk, arcs, atomics, slots, pulled);
+        else if (pp.work)
+            peel::run_async<Off, kPeelRepair>(pp, dom, s_tmp, st, clk, arcs, atomics, extra);
         else
             peel::run<Off, GridDom, kPeelRepair>(pp, dom, s_tmp, st, clk, arcs, atomics, extra);
     }
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 size_t hybrid_ws_bytes(long long n, long long m)
 {
-    const size_t a = peelone_ws_bytes(n, m), b = histocore_ws_bytes(n, m);
+    const size_t a = peelone_ws_bytes(n, m, true), b = histocore_ws_bytes(n, m);
     return a > b ? a : b;   // the two methods' scratch overlaps: only one runs
 }
 
@@ -90,20 +92,24 @@ template <typename Off>
 int launch_hybrid(const Off *rp, const int *ci, long long n, long long m, int *core, void *ws,
                   LastResult *last, cudaStream_t stream, const LaunchCfg &cfg)
 {
+    static int occ[64] = {};
+    int &o = occ[cfg.device & 63];
+    if (o == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hybrid_kernel<Off>, kThreads, 0) !=
+                cudaSuccess ||
+            o <= 0)
+            return -3;
+    }
+    const int per_sm = o < cfg.max_blocks_per_sm ? o : cfg.max_blocks_per_sm;
+    const int ctas = cfg.sms * per_sm;
     peel::Params<Off> pp;
     histo::Params<Off> hp;
     {
         Carver c(ws);
+        peel::carve(pp, c, n, m, cfg.peel_async && ctas <= peel::kMaxAsyncCtas);
         pp.rp = rp;
         pp.ci = ci;
-        pp.n = n;
         pp.core = core;
-        pp.ctl = c.take<Ctrl>(1);
-        pp.res0 = c.take<int>(n);
-        pp.res1 = c.take<int>(n);
-        pp.qs = c.take<int>(n);
-        pp.qb_cap = (unsigned)chunk_capacity(m);
-        pp.qb = c.take<int2>(pp.qb_cap);
         pp.tn = cfg.tn;
     }
     {
@@ -134,18 +140,9 @@ int launch_hybrid(const Off *rp, const int *ci, long long n, long long m, int *c
         hp.tn = cfg.tn;
     }
     if (cudaMemsetAsync(pp.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
-    static int occ[64] = {};
-    int &o = occ[cfg.device & 63];
-    if (o == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hybrid_kernel<Off>, kThreads, 0) !=
-                cudaSuccess ||
-            o <= 0)
-            return -3;
-    }
-    const int per_sm = o < cfg.max_blocks_per_sm ? o : cfg.max_blocks_per_sm;
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&pp, &hp, &last, &limit};
-    if (cudaLaunchCooperativeKernel((const void *)hybrid_kernel<Off>, dim3(cfg.sms * per_sm),
+    if (launch_cooperative((const void *)hybrid_kernel<Off>, dim3(ctas),
                                     dim3(kThreads), args, 0, stream) != cudaSuccess)
         return -3;
     return 0;

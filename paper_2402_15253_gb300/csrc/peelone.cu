@@ -1,5 +1,7 @@
 // PeelOne (Sec. III, Alg. 4) on one graph as one persistent cooperative
-// kernel: the algorithm body is peel::run (peelone.cuh) over the whole grid.
+// kernel: the algorithm body is peel::run_async (peelone.cuh) over the whole
+// grid, or peel::run (a grid barrier per frontier wave) when asynchronous
+// levels are switched off.
 #include "peelone.cuh"
 #include "pico.h"
 #include "pico_launch.h"
@@ -7,7 +9,7 @@
 namespace pico {
 namespace {
 
-template <typename Off, int Mode>
+template <typename Off, int Mode, bool kAsync>
 __global__ void __launch_bounds__(kThreads, 2)
     peelone_kernel(peel::Params<Off> p, LastResult *last, unsigned long long limit_ns)
 {
@@ -26,7 +28,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     clk.start();
     GridDom dom{p.ctl, s_snap, limit_ns};
-    peel::run<Off, GridDom, Mode>(p, dom, s_tmp, st, clk, arcs, atomics, extra);
+    if (kAsync)
+        peel::run_async<Off, Mode>(p, dom, s_tmp, st, clk, arcs, atomics, extra);
+    else
+        peel::run<Off, GridDom, Mode>(p, dom, s_tmp, st, clk, arcs, atomics, extra);
     block_sum_to(arcs, &p.ctl->stats[kStArcs], s_red);
     block_sum_to(atomics, &p.ctl->stats[kStAtomics], s_red);
     block_sum_to(extra, &p.ctl->stats[kStExtra], s_red);
@@ -39,20 +44,13 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 }  // namespace
 
-size_t chunk_capacity(long long m)
-{
-    // enough for every allowed tuning (chunk >= kMinChunk, small_deg >= kMinSmallDeg)
-    return (size_t)(m / kMinChunk + m / (kMinSmallDeg + 1) + 2);
-}
+size_t chunk_capacity(long long m) { return peel::chunk_list_capacity(m); }
 
-size_t peelone_ws_bytes(long long n, long long m)
+size_t peelone_ws_bytes(long long n, long long m, bool async)
 {
     Carver c(nullptr);
-    c.take<Ctrl>(1);
-    c.take<int>(n);
-    c.take<int>(n);
-    c.take<int>(n);
-    c.take<int2>(chunk_capacity(m));
+    peel::Params<int> p;
+    peel::carve(p, c, n, m, async);
     return c.size();
 }
 
@@ -60,38 +58,39 @@ template <typename Off>
 int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *core, void *ws,
                    LastResult *last, cudaStream_t stream, const LaunchCfg &cfg, int mode)
 {
-    Carver c(ws);
-    peel::Params<Off> p;
-    p.rp = rp;
-    p.ci = ci;
-    p.n = n;
-    p.core = core;
-    p.ctl = c.take<Ctrl>(1);
-    p.res0 = c.take<int>(n);
-    p.res1 = c.take<int>(n);
-    p.qs = c.take<int>(n);
-    p.qb_cap = (unsigned)chunk_capacity(m);
-    p.qb = c.take<int2>(p.qb_cap);
-    p.tn = cfg.tn;
-    if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
-
     if (mode < kPeelRepair || mode > kPeelAddBack) return -1;
-    const void *fns[3] = {(const void *)peelone_kernel<Off, kPeelRepair>,
-                          (const void *)peelone_kernel<Off, kPeelCas>,
-                          (const void *)peelone_kernel<Off, kPeelAddBack>};
-    static int occ[3][64] = {};
-    int &o = occ[mode][cfg.device & 63];
+    const void *fns[2][3] = {{(const void *)peelone_kernel<Off, kPeelRepair, false>,
+                              (const void *)peelone_kernel<Off, kPeelCas, false>,
+                              (const void *)peelone_kernel<Off, kPeelAddBack, false>},
+                             {(const void *)peelone_kernel<Off, kPeelRepair, true>,
+                              (const void *)peelone_kernel<Off, kPeelCas, true>,
+                              (const void *)peelone_kernel<Off, kPeelAddBack, true>}};
+    static int occ[2][3][64] = {};
+    bool async = cfg.peel_async;
+    int &o = occ[async][mode][cfg.device & 63];
     if (o == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[mode], kThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[async][mode], kThreads, 0) !=
                 cudaSuccess ||
             o <= 0)
             return -3;
     }
     const int per_sm = o < cfg.max_blocks_per_sm ? o : cfg.max_blocks_per_sm;
-    dim3 grid(cfg.sms * per_sm), block(kThreads);
+    const int ctas = cfg.sms * per_sm;
+    if (ctas > peel::kMaxAsyncCtas) async = false;   // the level-end flags have no room
+
+    Carver c(ws);
+    peel::Params<Off> p;
+    peel::carve(p, c, n, m, async);
+    p.rp = rp;
+    p.ci = ci;
+    p.core = core;
+    p.tn = cfg.tn;
+    if (cudaMemsetAsync(p.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
+
+    dim3 grid(ctas), block(kThreads);
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&p, &last, &limit};
-    if (cudaLaunchCooperativeKernel(fns[mode], grid, block, args, 0, stream) != cudaSuccess)
+    if (launch_cooperative(fns[async][mode], grid, block, args, 0, stream) != cudaSuccess)
         return -3;
     return 0;
 }

@@ -82,7 +82,8 @@ enum StatIdx : int {
 enum PhaseKind : int {
     kPhInit = 0, kPhScan, kPhWaveTiny, kPhWaveMid, kPhWaveWide, kPhInitHisto, kPhSumHisto,
     kPhUpdateHisto,
-    kPhUpdatePull   // trace only: counted as kPhUpdateHisto in the statistics
+    kPhUpdatePull,  // trace only: counted as kPhUpdateHisto in the statistics
+    kPhLevel        // trace only: one asynchronous PeelOne level, counted as kPhWaveWide
 };
 
 
@@ -139,7 +140,8 @@ struct PhaseClock {
     {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const unsigned long long t = gtime();
-            const int sk = kind > kPhUpdateHisto ? kPhUpdateHisto : kind;
+            const int sk =
+                kind == kPhLevel ? kPhWaveWide : (kind > kPhUpdateHisto ? kPhUpdateHisto : kind);
             st[kStPhaseNs + sk] += t - t_prev;
             st[kStPhaseCount + sk] += 1;
             if (trace && *trace_len < (unsigned)kTraceCap) {
@@ -177,6 +179,39 @@ __device__ __forceinline__ int ld_relaxed(const int *p)
     return v;
 }
 
+__device__ __forceinline__ int2 ld_relaxed(const int2 *p)
+{
+    int2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.s32 {%0, %1}, [%2];"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(int *p, int v)
+{
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed(int2 *p, int2 v)
+{
+    asm volatile("st.relaxed.gpu.global.v2.s32 [%0], {%1, %2};" ::"l"(p), "r"(v.x), "r"(v.y)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Mutable device data written by other CTAs is read through L2 only.
 __device__ __forceinline__ int ldcg(const int *p) { return __ldcg(p); }
 
@@ -206,8 +241,18 @@ __device__ __forceinline__ int status_of(Ctrl *c)
 // for that word with acquire loads (bounded: limit_ns and the status word)
 // and read the snapshot. A snapshot of parity p is rewritten two barriers
 // later, which every reader must reach first.
-static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap,
-                                              unsigned long long limit_ns, unsigned gen)
+// grid_sync_hook is the same barrier with `hook(live)` run by the last arrival
+// on the live counters it has loaded, before it publishes the snapshot and
+// releases the others: the hook's stores (relaxed, global) are visible to
+// every CTA after the barrier.
+struct NoHook {
+    __device__ __forceinline__ void operator()(const uint4 *) const {}
+};
+
+template <typename Hook>
+__device__ __forceinline__ bool grid_sync_hook(Ctrl *c, unsigned *s_snap,
+                                               unsigned long long limit_ns, unsigned gen,
+                                               const Hook &hook)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -224,6 +269,7 @@ static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap,
             uint4 t[kLiveWords / 4];
 #pragma unroll
             for (int i = 0; i < kLiveWords / 4; ++i) t[i] = __ldcg(live + i);
+            hook(t);
 #pragma unroll
             for (int i = 0; i < kLiveWords / 4; ++i) __stcg(snap + i, t[i]);
             st_release(&c->gen.w[0], gen + 1);
@@ -252,6 +298,12 @@ static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap,
     }
     __syncthreads();
     return s_snap[kLiveWords] == 0;
+}
+
+static __device__ __noinline__ bool grid_sync(Ctrl *c, unsigned *s_snap,
+                                              unsigned long long limit_ns, unsigned gen)
+{
+    return grid_sync_hook(c, s_snap, limit_ns, gen, NoHook{});
 }
 
 // Called once by every CTA at the end of a persistent kernel: folds the CTA's
@@ -380,6 +432,7 @@ __device__ __forceinline__ void warp_fill_chunks(unsigned nch, unsigned pos, int
 // Warp-cooperative append of the chunk entries of large vertices: every
 // lane with `pred` owns vertex v of degree d; the whole warp writes the
 // ceil(d / chunk) entries of each such vertex in turn.
+template <bool kRelaxedStores = false>
 __device__ __forceinline__ void warp_push_chunks(bool pred, int v, long long d, int2 *list,
                                                  unsigned *counter, unsigned cap, Ctrl *ctl,
                                                  int chunk)
@@ -399,7 +452,10 @@ __device__ __forceinline__ void warp_push_chunks(bool pred, int v, long long d, 
             if (lane == 0) set_error(ctl, kErrNotConverged);
             continue;
         }
-        for (unsigned c = lane; c < nch; c += 32) list[pos + c] = make_int2(vv, (int)c);
+        for (unsigned c = lane; c < nch; c += 32) {
+            if (kRelaxedStores) st_relaxed(list + pos + c, make_int2(vv, (int)c));
+            else list[pos + c] = make_int2(vv, (int)c);
+        }
     }
 }
 
@@ -438,85 +494,119 @@ __device__ __forceinline__ unsigned batch_width(unsigned nsmall, unsigned nbig, 
     return vb;
 }
 
+// One warp walks the concatenated adjacency of up to 32 small vertices, one
+// per lane (v < 0: no vertex; a vertex of degree above max_deg is skipped,
+// its arcs being listed as chunks elsewhere): a warp prefix sum of the
+// degrees and a 5-step shuffle search give each arc's owner; every lane
+// issues U arcs per step.
+template <typename Off, typename F>
+__device__ __forceinline__ void walk_batch(const int *__restrict__ ci, int v, Off rs, int d, F &f);
+
+template <typename Off, typename F>
+__device__ __forceinline__ void walk_small_batch(const Off *__restrict__ rp,
+                                                 const int *__restrict__ ci, int v, F &f,
+                                                 int max_deg)
+{
+    int d = 0;
+    Off rs = 0;
+    if (v >= 0) {
+        rs = rp[v];
+        const Off dd = rp[v + 1] - rs;
+        if (dd <= max_deg) d = (int)dd;
+    }
+    walk_batch(ci, v, rs, d, f);
+}
+
+// The same walk with each lane's row start rs = row_ptr[v] and the number d
+// of its arcs to walk given (d = 0: none).
+template <typename Off, typename F>
+__device__ __forceinline__ void walk_batch(const int *__restrict__ ci, int v, Off rs, int d, F &f)
+{
+    constexpr int U = F::kArcs;
+    const int lane = threadIdx.x & 31;
+    int a = 0, b = 0;
+    if (d > 0 && !f.item(v, a, b)) d = 0;
+    int incl = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - d;
+    const int T = __shfl_sync(kFull, incl, 31);
+    for (int base = 0; base < T; base += 32 * U) {
+        bool valid[U];
+        int vo[U], u[U], ao[U], bo[U];
+        Off rso[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const int fidx = base + 32 * j + lane;
+            int o = 0;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const int ex = __shfl_sync(kFull, excl, o + s);
+                if (ex <= fidx) o += s;
+            }
+            vo[j] = __shfl_sync(kFull, v, o);
+            rso[j] = __shfl_sync(kFull, rs, o);
+            const int exo = __shfl_sync(kFull, excl, o);
+            ao[j] = __shfl_sync(kFull, a, o);
+            bo[j] = __shfl_sync(kFull, b, o);
+            valid[j] = fidx < T;
+            u[j] = valid[j] ? __ldg(ci + rso[j] + (fidx - exo)) : -1;
+        }
+        f.arcs(valid, vo, u, rso, ao, bo);
+    }
+}
+
+// One warp walks chunk `c` (tn.chunk arcs) of the adjacency of vertex v.
+template <typename Off, typename F>
+__device__ __forceinline__ void walk_chunk(const Off *__restrict__ rp, const int *__restrict__ ci,
+                                           int v, int c, F &f, const Tuning &tn)
+{
+    constexpr int U = F::kArcs;
+    const int lane = threadIdx.x & 31;
+    const Off rs = rp[v], re = rp[v + 1];
+    const Off s = rs + (Off)c * tn.chunk;
+    const Off t = (s + tn.chunk < re) ? s + tn.chunk : re;
+    int a = 0, b = 0;
+    if (!f.item(v, a, b)) return;
+    for (Off e0 = s; e0 < t; e0 += 32 * U) {
+        bool valid[U];
+        int vo[U], u[U], ao[U], bo[U];
+        Off rso[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const Off e = e0 + 32 * j + lane;
+            valid[j] = e < t;
+            u[j] = valid[j] ? __ldg(ci + e) : -1;
+            vo[j] = v;
+            rso[j] = rs;
+            ao[j] = a;
+            bo[j] = b;
+        }
+        f.arcs(valid, vo, u, rso, ao, bo);
+    }
+}
+
 template <typename Off, typename F>
 __device__ __forceinline__ void expand(const Off *__restrict__ rp, const int *__restrict__ ci,
                                        const int *small, unsigned nsmall, const int2 *big,
                                        unsigned nbig, unsigned gwarp, unsigned nwarps, F &f,
                                        const Tuning &tn, unsigned vb = 32u)
 {
-    constexpr int U = F::kArcs;
     const int lane = threadIdx.x & 31;
     const unsigned nbatch = (nsmall + vb - 1u) / vb;
     const unsigned total = nbatch + nbig;
     for (unsigned unit = gwarp; unit < total; unit += nwarps) {
         if (unit < nbatch) {
             const unsigned idx = unit * vb + lane;
-            int v = -1, d = 0, a = 0, b = 0;
-            Off rs = 0;
-            if ((unsigned)lane < vb && idx < nsmall) {
-                v = small ? ldcg(small + idx) : (int)idx;
-                rs = rp[v];
-                const Off dd = rp[v + 1] - rs;
-                if (dd <= tn.small_deg) {
-                    d = (int)dd;
-                    if (d > 0 && !f.item(v, a, b)) d = 0;
-                }
-            }
-            int incl = d;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int excl = incl - d;
-            const int T = __shfl_sync(kFull, incl, 31);
-            for (int base = 0; base < T; base += 32 * U) {
-                bool valid[U];
-                int vo[U], u[U], ao[U], bo[U];
-                Off rso[U];
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const int fidx = base + 32 * j + lane;
-                    int o = 0;
-#pragma unroll
-                    for (int s = 16; s > 0; s >>= 1) {
-                        const int ex = __shfl_sync(kFull, excl, o + s);
-                        if (ex <= fidx) o += s;
-                    }
-                    vo[j] = __shfl_sync(kFull, v, o);
-                    rso[j] = __shfl_sync(kFull, rs, o);
-                    const int exo = __shfl_sync(kFull, excl, o);
-                    ao[j] = __shfl_sync(kFull, a, o);
-                    bo[j] = __shfl_sync(kFull, b, o);
-                    valid[j] = fidx < T;
-                    u[j] = valid[j] ? __ldg(ci + rso[j] + (fidx - exo)) : -1;
-                }
-                f.arcs(valid, vo, u, rso, ao, bo);
-            }
+            int v = -1;
+            if ((unsigned)lane < vb && idx < nsmall) v = small ? ldcg(small + idx) : (int)idx;
+            walk_small_batch(rp, ci, v, f, tn.small_deg);
         } else {
             const int2 ent = __ldcg(big + (unit - nbatch));   // written by other CTAs
-            const int v = ent.x;
-            const Off rs = rp[v], re = rp[v + 1];
-            const Off s = rs + (Off)ent.y * tn.chunk;
-            const Off t = (s + tn.chunk < re) ? s + tn.chunk : re;
-            int a = 0, b = 0;
-            if (!f.item(v, a, b)) continue;
-            for (Off e0 = s; e0 < t; e0 += 32 * U) {
-                bool valid[U];
-                int vo[U], u[U], ao[U], bo[U];
-                Off rso[U];
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const Off e = e0 + 32 * j + lane;
-                    valid[j] = e < t;
-                    u[j] = valid[j] ? __ldg(ci + e) : -1;
-                    vo[j] = v;
-                    rso[j] = rs;
-                    ao[j] = a;
-                    bo[j] = b;
-                }
-                f.arcs(valid, vo, u, rso, ao, bo);
-            }
+            walk_chunk(rp, ci, ent.x, ent.y, f, tn);
         }
     }
 }
@@ -709,6 +799,11 @@ struct GridDom {
     static constexpr bool kGrid = true;
     __device__ __forceinline__ unsigned *live() const { return ctl->live.w; }
     __device__ __forceinline__ bool sync() { return grid_sync(ctl, s_snap, limit_ns, gen++); }
+    template <typename Hook>
+    __device__ __forceinline__ bool sync_hook(const Hook &h)
+    {
+        return grid_sync_hook(ctl, s_snap, limit_ns, gen++, h);
+    }
     __device__ __forceinline__ unsigned tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ __forceinline__ unsigned nthreads() const { return gridDim.x * blockDim.x; }
     __device__ __forceinline__ unsigned cta() const { return blockIdx.x; }

@@ -20,7 +20,27 @@ struct LaunchCfg {
     unsigned long long limit_ns;   // time limit of every device-side wait
     Tuning tn;                     // degree-class work assignment
     int batched_threads;           // threads per CTA of the batched kernel (256 or 512)
+    bool peel_async = false;       // single-graph PeelOne: asynchronous levels (run_async)
 };
+
+// Launches a persistent kernel whose CTAs must all be resident at once (its
+// grid barrier waits for every CTA): a cooperative launch, made through
+// cudaLaunchKernelExC so that a stream capture can record it in a CUDA graph.
+inline cudaError_t launch_cooperative(const void *fn, dim3 grid, dim3 block, void **args,
+                                      size_t smem, cudaStream_t stream)
+{
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelExC(&lc, fn, args);
+}
 
 // Sub-buffer carving of a scratch allocation (256-byte aligned pieces).
 struct Carver {
@@ -42,7 +62,8 @@ struct Carver {
 // vertex of degree > kSmallDeg contributes ceil(deg / kChunk) entries.
 size_t chunk_capacity(long long m);
 
-size_t peelone_ws_bytes(long long n, long long m);
+// async: with the arrays of asynchronous levels (peel::run_async)
+size_t peelone_ws_bytes(long long n, long long m, bool async = false);
 size_t histocore_ws_bytes(long long n, long long m);
 
 // mode: kPeelRepair (PeelOne), kPeelCas or kPeelAddBack (ablations)

@@ -33,7 +33,7 @@ int selftest_wait_timeout(LastResult *last, int limit_ms, cudaStream_t stream, c
     if (cudaMemsetAsync(ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) rc = -3;
     unsigned long long limit = (unsigned long long)limit_ms * 1000000ull;
     void *args[] = {&ctl, &last, &limit};
-    if (rc == 0 && cudaLaunchCooperativeKernel((const void *)wait_timeout_kernel, dim3(cfg.sms),
+    if (rc == 0 && launch_cooperative((const void *)wait_timeout_kernel, dim3(cfg.sms),
                                                dim3(256), args, 0, stream) != cudaSuccess)
         rc = -3;
     cudaFreeAsync(ctl, stream);

@@ -56,7 +56,8 @@ def test_auto_picks_by_rule_and_matches_oracle(pico, name, make, want_method):
         assert st["rounds"] == ost["rounds"] and st["frontier"] == ost["frontier"]
     else:
         _, ost = oracle.peelone(rp, ci)
-        assert st["levels"] == ost["levels"] and st["subrounds"] == ost["waves"]
+        assert st["levels"] == ost["levels"] and st["arcs"] == ost["arcs_scanned"]
+        assert st["atomics"] - st["extra"] == ost["decrements"]
 
 
 def test_auto_int64_offsets(pico):

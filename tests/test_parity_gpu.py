@@ -2,9 +2,18 @@
 
 Coreness is a unique integer vector, so every comparison is exact (bit for
 bit). The renditions of Alg. 4 and Alg. 6 in the oracle also fix the
-iteration structure: the GPU's non-empty levels, frontier waves and
-HistoCore rounds must equal theirs.
+iteration structure: the GPU's non-empty levels, arcs walked and successful
+decrements (PeelOne) and rounds (HistoCore) must equal theirs. PeelOne
+processes each level's dynamic frontier asynchronously, so the waves of the
+sequential rendition are not a GPU quantity there: Thm. 1 and Cor. 1 make
+the result independent of the order within a level. The per-wave form (every
+wave ended by a grid barrier, switched on with PICO_PEEL_WAVES=1) must match
+the waves too.
 """
+import os
+import subprocess
+import sys
+
 import itertools
 
 import numpy as np
@@ -54,7 +63,9 @@ def test_g1(pico, algo):
     got, st = run(pico, gg.from_edge_list(edges, n), algo)
     assert got.tolist() == want
     if algo == "peelone":
-        assert st["levels"] == 2 and st["kmax"] == 2 and st["subrounds"] == 3
+        assert st["levels"] == 2 and st["kmax"] == 2
+        # level 1 lowers v5 twice (v0, v1); level 2 lowers v3 and v5 once each
+        assert st["arcs"] == 14 and st["atomics"] - st["extra"] == 4
     else:
         assert st["rounds"] == 1 and st["frontier"] == 2
 
@@ -150,8 +161,8 @@ def test_families_match_oracle(pico, algo, name, make):
         _, ost = oracle.peelone(rp, ci)
         assert st["levels"] == ost["levels"]
         assert st["kmax"] == ost["kmax"]
-        assert st["subrounds"] == ost["waves"]
         assert st["arcs"] == ost["arcs_scanned"]
+        assert st["atomics"] - st["extra"] == ost["decrements"]
     else:
         _, ost = oracle.histocore(rp, ci)
         assert st["rounds"] == ost["rounds"]
@@ -277,3 +288,37 @@ def test_full_size_workloads(pico, name):
         assert (want[members] >= 2999).all()
     if name == "grid4096":
         assert (want == 2).all()
+
+
+_WAVES_CHILD = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import torch
+import graphgen as gg
+import oracle
+import paper_2402_15253_gb300 as pico
+torch.cuda.set_device(0)
+bad = 0
+for g in (gg.workload("rmat16"), gg.chung_lu_graph(1 << 16, 33, clique=300),
+          gg.grid_graph(257, 333), gg.path_graph(5000)):
+    rp, ci = g.numpy()
+    out = pico.coreness(g.row_ptr.cuda(), g.col_idx.cuda(), "peelone").cpu().numpy()
+    st = pico.pico_get_stats()
+    _, ost = oracle.peelone(rp, ci)
+    ok = (np.array_equal(out, oracle.bz_coreness(rp, ci)) and st["levels"] == ost["levels"]
+          and st["subrounds"] == ost["waves"] and st["arcs"] == ost["arcs_scanned"])
+    bad += not ok
+print("BAD", bad)
+"""
+
+
+def test_peelone_per_wave_form_matches_oracle_waves():
+    """PICO_PEEL_WAVES=1 selects the form that ends every wave of the dynamic
+    frontier with a grid barrier: results, levels and waves are the oracle's."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _WAVES_CHILD, root],
+                       env=dict(os.environ, PICO_PEEL_WAVES="1"), capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "BAD 0" in r.stdout, r.stdout[-2000:]
