@@ -558,6 +558,32 @@ def bench_configs(pico, dev, stream, names=("rmat16", "rmat22", "chunglu24", "gr
     return res
 
 
+def bench_partitioned(pico, g, ref, parts=(2, 4), reps: int = 3):
+    """Partitioned HistoCore (pico_coreness_partitioned) on the workload graph
+    with P equal vertex ranges on this GPU: wall time of the whole call (it
+    synchronises once per phase of every round), the median of `reps` runs
+    after one warm-up; the result must equal the single-kernel one."""
+    import torch
+    rp = g.row_ptr.to(torch.int64)
+    res = {"note": "every round: SumHisto in each partition, an exchange of the change "
+                   "records, UpdateHisto pulled into each partition's rows; host-driven"}
+    for P in parts:
+        out, rounds = pico.coreness_partitioned(rp, g.col_idx, P)
+        if not torch.equal(out, ref):
+            raise AssertionError(f"partitioned HistoCore with {P} parts differs")
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pico.coreness_partitioned(rp, g.col_idx, P, out=out)
+            torch.cuda.synchronize()
+            times.append(1000.0 * (time.perf_counter() - t0))
+        ms = statistics.median(times)
+        res[str(P)] = {"ms": ms, "rounds": rounds, "edges_per_s": g.arcs / 2 / (ms / 1e3)}
+    del rp
+    return res
+
+
 def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6,
                       update_tuning=None, recompute_tuning=None):
     """Core maintenance on the workload graph: batches of k random edge
@@ -734,6 +760,8 @@ def main():
                          "(or PeelOne's/HistoCore's, separated by '/')")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the served-form measurement (0: skip)")
+    ap.add_argument("--no-partitioned", action="store_true",
+                    help="skip partitioned HistoCore on the workload graph")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the per-workload record of the other single-graph workloads")
     args = ap.parse_args()
@@ -963,6 +991,8 @@ def main():
             recompute_tuning=tuned[line["auto"]["method"]] if rank == 0 else None)
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)
+    if rank == 0 and not args.no_partitioned:
+        line["partitioned"] = bench_partitioned(pico, g, out["histocore"])
     if rank == 0 and args.serve_requests > 0:
         line["served"] = bench_serve(pico, dev, args.serve_requests)
     h_csr = None   # host copy of the workload graph for the CPU baseline

@@ -335,6 +335,63 @@ int pico_dyn_graph(pico_dyn *d, const int64_t **row_ptr, const int32_t **col_idx
 int pico_dyn_copy_graph(pico_dyn *d, int64_t *row_ptr, int32_t *col_idx, pico_stream_t stream);
 void pico_dyn_destroy(pico_dyn *d);
 
+/*
+ * Partitioned HistoCore: Alg. 6 over a graph whose vertices are split into
+ * contiguous ranges, each held by one partition (Index2core's fit to a
+ * distributed setting, Sec. VI; multi-GPU processing is future work in Sec.
+ * VII). A round runs SumHisto in every partition, then every partition
+ * receives every partition's change records of the round and pulls the
+ * UpdateHisto edits into its own rows; the rounds, the histograms and the
+ * result equal those of the single-graph HistoCore. Partitions only meet in
+ * the exchange, which the caller performs between calls, so they can live on
+ * different devices or processes (the exchange is then an all-gather).
+ *
+ * pico_part_create sets up the partition of rows [lo, hi) of a graph given by
+ * row_ptr (int64, n + 1 entries) and col_idx (device memory, read only; only
+ * the partition's rows of col_idx are read), runs InitHisto and lists its
+ * initial V_cnt; it synchronises `stream` and returns NULL on invalid
+ * arguments (0 <= lo < hi <= n required) or failure. The partition owns its
+ * device memory (estimates, histograms, lists, and an n-entry {old, new}
+ * array) until pico_part_destroy.
+ *
+ * pico_part_sum runs SumHisto over the partition's V_cnt and reports the
+ * number of records of the round (*n_changed; 0 when its V_cnt was empty)
+ * and their smallest new estimate (*ymin, INT32_MAX when none). The records
+ * are 3 int32 each, (vertex, old estimate, new estimate), at
+ * pico_part_records(p) (device memory, valid until the next pico_part_sum);
+ * pico_part_copy_records enqueues their copy to dst (device memory, room for
+ * 3 * n_changed int32) on `stream`.
+ *
+ * pico_part_apply takes the round's records of ALL partitions (device
+ * memory, 3 * count int32, any order) and the smallest new estimate over all
+ * of them, applies the UpdateHisto edits to the partition's rows and lists
+ * its next V_cnt (*next_vcnt vertices). The computation is over when a round
+ * has no records in any partition. Both calls synchronise `stream` and return
+ * PICO_OK, PICO_ERR_INVALID_ARG, PICO_ERR_BAD_GRAPH (a record or a sum that
+ * an invalid graph produces) or PICO_ERR_CUDA.
+ *
+ * pico_part_coreness copies the partition's estimates (hi - lo int32, device
+ * memory) to out_core; after the last round they are the coreness.
+ *
+ * pico_coreness_partitioned runs the whole computation on the current device
+ * with `parts` partitions of equal vertex ranges, moving the records between
+ * them itself; *rounds (if not NULL) receives the number of rounds. It
+ * synchronises `stream`. row_ptr is int64 (n + 1), col_idx has m entries.
+ */
+typedef struct pico_part pico_part;
+pico_part *pico_part_create(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t lo,
+                            int64_t hi, pico_stream_t stream);
+int pico_part_sum(pico_part *p, int64_t *n_changed, int32_t *ymin, pico_stream_t stream);
+const int32_t *pico_part_records(pico_part *p);
+int pico_part_copy_records(pico_part *p, int32_t *dst, pico_stream_t stream);
+int pico_part_apply(pico_part *p, const int32_t *records, int64_t count, int32_t ymin,
+                    int64_t *next_vcnt, pico_stream_t stream);
+int pico_part_coreness(pico_part *p, int32_t *out_core, pico_stream_t stream);
+void pico_part_destroy(pico_part *p);
+int pico_coreness_partitioned(const int64_t *row_ptr, const int32_t *col_idx, int64_t n,
+                              int64_t m, int32_t *out_core, int32_t parts, int64_t *rounds,
+                              pico_stream_t stream);
+
 /* Direction of HistoCore's UpdateHisto (Sec. IV-B, Alg. 6). */
 #define PICO_UPDATE_AUTO 0   /* per round: pull when the round's changed vertices hold at
                                 least pull_pct % of the arcs of a graph with >= 2^22 arcs */

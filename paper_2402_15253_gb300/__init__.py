@@ -151,6 +151,22 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_get_trace.restype = i32
     L.pico_coreness_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     L.pico_coreness_noalloc.restype = i32
+    L.pico_part_create.argtypes = [vp, vp, i64, i64, i64, vp]
+    L.pico_part_create.restype = vp
+    L.pico_part_sum.argtypes = [vp, vp, vp, vp]
+    L.pico_part_sum.restype = i32
+    L.pico_part_records.argtypes = [vp]
+    L.pico_part_records.restype = vp
+    L.pico_part_copy_records.argtypes = [vp, vp, vp]
+    L.pico_part_copy_records.restype = i32
+    L.pico_part_apply.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.pico_part_apply.restype = i32
+    L.pico_part_coreness.argtypes = [vp, vp, vp]
+    L.pico_part_coreness.restype = i32
+    L.pico_part_destroy.argtypes = [vp]
+    L.pico_part_destroy.restype = None
+    L.pico_coreness_partitioned.argtypes = [vp, vp, i64, i64, vp, i32, vp, vp]
+    L.pico_coreness_partitioned.restype = i32
     _lib = L
     return L
 
@@ -237,6 +253,123 @@ def pico_coreness_noalloc(row_ptr, col_idx, n: int, m: int, out_core, out_status
 PICO_NOALLOC_MAX_VERTICES = 1 << 20
 PICO_NOALLOC_MAX_ARCS = 1 << 24
 
+
+def pico_coreness_partitioned(row_ptr, col_idx, n: int, m: int, out_core, parts: int,
+                              rounds=None, stream=None) -> int:
+    return load().pico_coreness_partitioned(_ptr(row_ptr), _ptr(col_idx), n, m, _ptr(out_core),
+                                            parts, _ptr(rounds), _stream(stream))
+
+
+def pico_part_create(row_ptr, col_idx, n: int, lo: int, hi: int, stream=None):
+    return load().pico_part_create(_ptr(row_ptr), _ptr(col_idx), n, lo, hi, _stream(stream))
+
+
+def pico_part_sum(part, n_changed, ymin, stream=None) -> int:
+    return load().pico_part_sum(part, n_changed, ymin, _stream(stream))
+
+
+def pico_part_records(part):
+    return load().pico_part_records(part)
+
+
+def pico_part_copy_records(part, dst, stream=None) -> int:
+    return load().pico_part_copy_records(part, _ptr(dst), _stream(stream))
+
+
+def pico_part_apply(part, records, count: int, ymin: int, next_vcnt, stream=None) -> int:
+    return load().pico_part_apply(part, _ptr(records), count, ymin, next_vcnt, _stream(stream))
+
+
+def pico_part_coreness(part, out_core, stream=None) -> int:
+    return load().pico_part_coreness(part, _ptr(out_core), _stream(stream))
+
+
+def pico_part_destroy(part) -> None:
+    load().pico_part_destroy(part)
+
+
+class Partition:
+    """One partition of partitioned HistoCore (pico_part_*): the rows
+    [lo, hi) of a graph held on the current device. sum() and apply() are the
+    two halves of a round; the exchange of records between partitions happens
+    between them (see paper_2402_15253_gb300.distributed)."""
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, lo: int, hi: int,
+                 stream=None):
+        if row_ptr.dtype != torch.int64 or col_idx.dtype != torch.int32:
+            raise TypeError("row_ptr must be int64 and col_idx int32")
+        self.device = row_ptr.device
+        self.lo, self.hi = lo, hi
+        self._keep = (row_ptr, col_idx)
+        self._stream = stream
+        self._h = pico_part_create(row_ptr, col_idx, row_ptr.numel() - 1, lo, hi, stream)
+        if not self._h:
+            raise PicoError(PICO_ERR_INVALID_ARG, "pico_part_create")
+
+    def sum(self):
+        """SumHisto over the partition's V_cnt: (records, ymin) with records
+        an int32 device tensor of 3 * count entries (vertex, old, new)."""
+        c, y = ctypes.c_int64(), ctypes.c_int32()
+        rc = pico_part_sum(self._h, ctypes.byref(c), ctypes.byref(y), self._stream)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_part_sum")
+        count = int(c.value)
+        if count == 0:
+            return torch.empty(0, dtype=torch.int32, device=self.device), int(y.value)
+        recs = torch.empty(3 * count, dtype=torch.int32, device=self.device)
+        rc = pico_part_copy_records(self._h, recs, self._stream)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_part_copy_records")
+        return recs, int(y.value)
+
+    def apply(self, records: torch.Tensor, ymin: int) -> int:
+        """The round's records of all partitions and their smallest new
+        estimate: applies the edits to the own rows; returns the next V_cnt
+        size."""
+        records = records.to(device=self.device, dtype=torch.int32).contiguous()
+        nxt = ctypes.c_int64()
+        rc = pico_part_apply(self._h, records, records.numel() // 3, ymin, ctypes.byref(nxt),
+                             self._stream)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_part_apply")
+        return int(nxt.value)
+
+    def coreness(self) -> torch.Tensor:
+        out = torch.empty(self.hi - self.lo, dtype=torch.int32, device=self.device)
+        rc = pico_part_coreness(self._h, out, self._stream)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_part_coreness")
+        torch.cuda.synchronize(self.device)
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            pico_part_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def coreness_partitioned(row_ptr: torch.Tensor, col_idx: torch.Tensor, parts: int,
+                         out: torch.Tensor | None = None, stream=None):
+    """Coreness by partitioned HistoCore with `parts` vertex ranges on the
+    current device; returns (coreness, rounds)."""
+    row_ptr = row_ptr.to(torch.int64).contiguous()
+    col_idx = col_idx.contiguous()
+    n = row_ptr.numel() - 1
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int32, device=row_ptr.device)
+    rounds = torch.zeros(1, dtype=torch.int64)
+    with torch.cuda.device(row_ptr.device):
+        rc = pico_coreness_partitioned(row_ptr, col_idx, n, col_idx.numel(), out, parts,
+                                       rounds.data_ptr(), stream)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_coreness_partitioned")
+    return out, int(rounds.item())
 
 
 def pico_workspace_bytes(n: int, m: int, algo: int) -> int:
