@@ -590,7 +590,9 @@ def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6,
     insertions (non-edges), k random deletions (existing edges) and both,
     each timed with CUDA events around pico_dyn_update, against a full
     recomputation (PICO_ALGO_AUTO) of the updated graph. The maintained
-    coreness must equal the recomputed one. The tunings (S, C, T, K) are set
+    coreness must equal the recomputed one. The state runs its default
+    policy: it recomputes instead of maintaining when its cost model
+    predicts that maintenance would take longer ("path"). The tunings (S, C, T, K) are set
     before each update and each recomputation (None: leave as is)."""
     import numpy as np
     import torch
@@ -669,6 +671,8 @@ def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6,
         if not torch.equal(full, dg.coreness()):
             raise AssertionError(f"maintained coreness differs after the {name} batch")
         res["runs"][name] = {"update_ms": e0.elapsed_time(e1),
+                             "path": ("recomputed" if dg.last_update_kind == pico.PICO_DYN_RECOMPUTED
+                                      else "maintained"),
                              "recompute_ms": r0.elapsed_time(r1),
                              "speedup": r0.elapsed_time(r1) / e0.elapsed_time(e1),
                              "stats": {x: st[x] for x in ("algo", "rounds", "frontier", "active", "subrounds",

@@ -336,6 +336,29 @@ int pico_dyn_copy_graph(pico_dyn *d, int64_t *row_ptr, int32_t *col_idx, pico_st
 void pico_dyn_destroy(pico_dyn *d);
 
 /*
+ * Recomputation fallback of pico_dyn_update (no counterpart in the paper).
+ * Under PICO_DYN_AUTO (the default) an update recomputes the coreness from
+ * scratch (PICO_ALGO_AUTO on the updated graph) instead of maintaining it
+ * when the batch's predicted maintenance time exceeds the last full
+ * computation's. The prediction scales the device time (measured with
+ * events) that the deletion step and the insertion passes took in the last
+ * batches that ran them by the ratio of edge counts, and is made only when
+ * those batches were within a factor of two of this one in size; otherwise
+ * the batch is maintained (and measured). PICO_DYN_MAINTAIN always
+ * maintains, PICO_DYN_RECOMPUTE always recomputes. The result is the same
+ * coreness either way. pico_dyn_last_update_kind reports what the last update
+ * did (PICO_DYN_MAINTAINED or PICO_DYN_RECOMPUTED; after a recomputation
+ * pico_get_stats describes the recomputing call).
+ */
+#define PICO_DYN_AUTO 0
+#define PICO_DYN_MAINTAIN 1
+#define PICO_DYN_RECOMPUTE 2
+#define PICO_DYN_MAINTAINED 0
+#define PICO_DYN_RECOMPUTED 1
+int pico_dyn_set_policy(pico_dyn *d, int policy);
+int pico_dyn_last_update_kind(pico_dyn *d);
+
+/*
  * Partitioned HistoCore: Alg. 6 over a graph whose vertices are split into
  * contiguous ranges, each held by one partition (Index2core's fit to a
  * distributed setting, Sec. VI; multi-GPU processing is future work in Sec.

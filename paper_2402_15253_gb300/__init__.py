@@ -141,6 +141,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_dyn_copy_graph.restype = i32
     L.pico_dyn_destroy.argtypes = [vp]
     L.pico_dyn_destroy.restype = None
+    L.pico_dyn_set_policy.argtypes = [vp, i32]
+    L.pico_dyn_set_policy.restype = i32
+    L.pico_dyn_last_update_kind.argtypes = [vp]
+    L.pico_dyn_last_update_kind.restype = i32
     L.pico_set_histo_update.argtypes = [i32, i32]
     L.pico_set_histo_update.restype = i32
     L.pico_get_histo_update.argtypes = [vp, vp]
@@ -436,6 +440,18 @@ def pico_dyn_copy_graph(d, row_ptr: torch.Tensor, col_idx: torch.Tensor, stream=
     return load().pico_dyn_copy_graph(d, _ptr(row_ptr), _ptr(col_idx), _stream(stream))
 
 
+PICO_DYN_AUTO, PICO_DYN_MAINTAIN, PICO_DYN_RECOMPUTE = 0, 1, 2
+PICO_DYN_MAINTAINED, PICO_DYN_RECOMPUTED = 0, 1
+
+
+def pico_dyn_set_policy(d, policy: int) -> int:
+    return load().pico_dyn_set_policy(d, policy)
+
+
+def pico_dyn_last_update_kind(d) -> int:
+    return load().pico_dyn_last_update_kind(d)
+
+
 def pico_dyn_destroy(d) -> None:
     load().pico_dyn_destroy(d)
 
@@ -471,6 +487,18 @@ class DynamicGraph:
             rc = pico_dyn_update(self._d, ins, ni, dele, nd, stream)
         if rc != PICO_OK:
             raise PicoError(rc, "pico_dyn_update")
+
+    def set_policy(self, policy: int) -> None:
+        """PICO_DYN_AUTO (maintain or recompute by the cost model),
+        PICO_DYN_MAINTAIN or PICO_DYN_RECOMPUTE."""
+        rc = pico_dyn_set_policy(self._d, policy)
+        if rc != PICO_OK:
+            raise PicoError(rc, "pico_dyn_set_policy")
+
+    @property
+    def last_update_kind(self) -> int:
+        """PICO_DYN_MAINTAINED or PICO_DYN_RECOMPUTED for the last update."""
+        return pico_dyn_last_update_kind(self._d)
 
     def coreness(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.n, dtype=torch.int32, device=self.device)

@@ -948,6 +948,13 @@ struct pico_dyn {
     int *core;
     int *cd;         // per vertex: neighbours of core >= own (insertion passes)
     bool cd_valid;   // cd matches the current graph and coreness
+    // Cost model of the recomputation fallback: device time of the last full
+    // computation, and the size and device time of the last batch that ran
+    // each maintenance step (deletions, insertions; size 0: none yet).
+    double full_ms = 0, del_ms = 0, ins_ms = 0;
+    long long del_k = 0, ins_k = 0;
+    int policy = PICO_DYN_AUTO;
+    int last_kind = PICO_DYN_MAINTAINED;
 };
 
 namespace {
@@ -958,6 +965,34 @@ unsigned pow2_at_least(long long x)
     while ((long long)p < x && p < (1u << 31)) p <<= 1;
     return p;
 }
+
+// Device time between two events recorded around work on one stream (the
+// stream is synchronised); negative when the events failed.
+struct EventTimer {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    EventTimer()
+    {
+        if (cudaEventCreate(&e[0]) != cudaSuccess || cudaEventCreate(&e[1]) != cudaSuccess)
+            cudaGetLastError();
+    }
+    ~EventTimer()
+    {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    void start(cudaStream_t s) { if (e[0]) cudaEventRecord(e[0], s); }
+    void stop(cudaStream_t s) { if (e[1]) cudaEventRecord(e[1], s); }
+    double ms()
+    {
+        float t = -1.0f;
+        if (!e[0] || !e[1] || cudaEventSynchronize(e[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.0;
+        }
+        return t;
+    }
+};
 
 int sync_status(cudaStream_t s)
 {
@@ -1053,9 +1088,12 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
                                cudaMemcpyDeviceToDevice, s) == cudaSuccess;
     ok = ok && (m == 0 || cudaMemcpyAsync(d->ci[0], col_idx, (size_t)m * sizeof(int),
                                           cudaMemcpyDeviceToDevice, s) == cudaSuccess);
+    EventTimer full;
+    full.start(s);
     ok = ok && pico_coreness_i64(reinterpret_cast<const int64_t *>(d->rp[0]), d->ci[0], n, m,
                                  d->core, PICO_ALGO_AUTO, stream) ==
                    PICO_OK;
+    full.stop(s);
     // cd for the first insertion batch: one count over all arcs
     void *ws = nullptr;
     ok = ok && cudaMallocAsync(&ws, pico::dyn::maint_ws_bytes(n, m), s) == cudaSuccess;
@@ -1068,6 +1106,7 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
         return nullptr;
     }
     d->cd_valid = true;
+    d->full_ms = full.ms();
     return d;
 }
 
@@ -1176,6 +1215,36 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     d->m = m_new;
     const bool cd_was_valid = d->cd_valid;
     d->cd_valid = false;   // until insertion passes leave it exact
+    // Maintain, or recompute from scratch when the batch's predicted
+    // maintenance time exceeds the last full computation's. A step's time
+    // is predicted from the last batch that ran it, scaled by the edge
+    // counts, only when the sizes are within a factor of two (a step's cost
+    // is not linear over a wider range); otherwise the batch is maintained
+    // and measured.
+    bool recompute = d->policy == PICO_DYN_RECOMPUTE;
+    if (d->policy == PICO_DYN_AUTO && d->full_ms > 0) {
+        auto near = [](long long k, long long k0) { return k0 > 0 && 2 * k >= k0 && k <= 2 * k0; };
+        const bool known = (n_del == 0 || near(n_del, d->del_k)) && (n_ins == 0 || near(n_ins, d->ins_k));
+        const double pred = (n_del ? d->del_ms * (double)n_del / (double)std::max(1ll, d->del_k) : 0.0) +
+                            (n_ins ? d->ins_ms * (double)n_ins / (double)std::max(1ll, d->ins_k) : 0.0);
+        recompute = known && pred > d->full_ms;
+    }
+    if (recompute) {
+        cudaFreeAsync(ws, s);
+        EventTimer full;
+        full.start(s);
+        rc = pico_coreness_i64(reinterpret_cast<const int64_t *>(nrp), nci, n, m_new, d->core,
+                               PICO_ALGO_AUTO, stream);
+        full.stop(s);
+        if (rc != PICO_OK) return rc;
+        if (sync_status(s) != PICO_OK) return PICO_ERR_CUDA;
+        const double t = full.ms();
+        if (t > 0) d->full_ms = t;
+        d->last_kind = PICO_DYN_RECOMPUTED;
+        return pico_last_device_status(stream);   // cd stays invalid: the next insertion
+    }                                             // batch recounts it
+    EventTimer tdel, tins;
+    tdel.start(s);
     if (n_del > 0 && m_new > 0) {
         rc = pico::launch_histocore<long long>(nrp, nci, n, m_new, d->core, ws2, last, s, cfg,
                                                d->core);
@@ -1183,9 +1252,12 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     } else if (n_del > 0) {
         ok = cudaMemsetAsync(d->core, 0, (size_t)n * sizeof(int), s) == cudaSuccess;
     }
+    tdel.stop(s);
+    tins.start(s);
     if (ok && n_ins > 0)
         ok = launch_maint(d, nrp, nci, m_new, ins, n_ins, cd_was_valid && n_del == 0, false, ws2,
                           s, cfg, last);
+    tins.stop(s);
     cudaFreeAsync(ws, s);
     if (!ok) {
         cudaGetLastError();
@@ -1194,7 +1266,32 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     if (sync_status(s) != PICO_OK) return PICO_ERR_CUDA;
     const int st = pico_last_device_status(stream);
     d->cd_valid = st == PICO_OK && n_ins > 0;
+    d->last_kind = PICO_DYN_MAINTAINED;
+    if (st == PICO_OK) {
+        const double a = tdel.ms(), b = tins.ms();
+        if (n_del > 0 && a > 0) {
+            d->del_ms = a;
+            d->del_k = n_del;
+        }
+        if (n_ins > 0 && b > 0) {
+            d->ins_ms = b;
+            d->ins_k = n_ins;
+        }
+    }
     return st;
+}
+
+int pico_dyn_set_policy(pico_dyn *d, int policy)
+{
+    if (!d || policy < PICO_DYN_AUTO || policy > PICO_DYN_RECOMPUTE) return PICO_ERR_INVALID_ARG;
+    d->policy = policy;
+    return PICO_OK;
+}
+
+int pico_dyn_last_update_kind(pico_dyn *d)
+{
+    if (!d) return PICO_ERR_INVALID_ARG;
+    return d->last_kind;
 }
 
 int pico_dyn_coreness(pico_dyn *d, int32_t *out_core, pico_stream_t stream)

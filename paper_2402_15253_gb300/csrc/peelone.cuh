@@ -734,8 +734,9 @@ __device__ void run_async(const Params<Off> &p, GridDom &dom, unsigned *s_tmp,
             }
             fin = __shfl_sync(kFull, fin, 0);
             if (fin) {   // the level's last listed entry has been walked
+                __threadfence();   // one fence, then plain strong stores: a release
                 for (unsigned c = lane; c < gridDim.x; c += 32)
-                    st_release(reinterpret_cast<int *>(p.actl[A_FLAGS + c].w), k);
+                    st_relaxed(reinterpret_cast<int *>(p.actl[A_FLAGS + c].w), k);
                 break;
             }
             if (__shfl_sync(kFull, over, 0)) {

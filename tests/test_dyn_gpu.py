@@ -219,3 +219,32 @@ def test_starting_from_no_edges(pico):
     dg.update(insert=[(0, 2), (2, 3)])
     check(pico, dg, n, {(0, 1), (1, 2), (0, 2), (2, 3)})
     assert dg.coreness().cpu().tolist() == [2, 2, 2, 1, 0, 0]
+
+
+@pytest.mark.parametrize("policy", ("recompute", "auto"))
+def test_recomputation_fallback(pico, policy):
+    """The fallback recomputes the coreness from scratch instead of
+    maintaining it; every batch must still give the oracle's coreness and
+    the exact edge set, and the next insertion batch after a recomputation
+    (whose insertion passes must recount their neighbour counts) too."""
+    rng = np.random.default_rng(61)
+    g = gg.rmat_graph(12, 8, 62)
+    n = g.n
+    edges = edges_of(g)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=2 * len(edges) + 20000)
+    pol = {"recompute": pico.PICO_DYN_RECOMPUTE, "auto": pico.PICO_DYN_AUTO}[policy]
+    kinds = []
+    for step, (ki, kd) in enumerate([(300, 0), (0, 300), (400, 400), (200, 0), (2000, 2000)]):
+        dg.set_policy(pol if step != 3 else pico.PICO_DYN_MAINTAIN)
+        ins, dele = random_batch(rng, n, edges, ki, kd)
+        dg.update(insert=ins, delete=dele)
+        edges = (edges - set(dele)) | set(ins)
+        check(pico, dg, n, edges)
+        kinds.append(dg.last_update_kind)
+    assert kinds[3] == pico.PICO_DYN_MAINTAINED   # insertion passes right after a recompute
+    if policy == "recompute":
+        assert kinds[:3] == [pico.PICO_DYN_RECOMPUTED] * 3 and kinds[4] == pico.PICO_DYN_RECOMPUTED
+    else:   # the first batch of each kind is maintained: its cost is not known yet,
+        # and so is the last, 5x larger than any earlier one
+        assert kinds[0] == pico.PICO_DYN_MAINTAINED and kinds[1] == pico.PICO_DYN_MAINTAINED
+        assert kinds[4] == pico.PICO_DYN_MAINTAINED
