@@ -405,7 +405,7 @@ def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int
 
 
 BYTES_MODEL = {
-    "peelone": "B_PeelOne = B_min + 4 B per decrement + 4 B per residual entry scanned, "
+    "peelone": "B_PeelOne = B_min + 4 B per successful decrement + 4 B per residual entry scanned, "
                "B_min = w_r(n+1) + 8 B/arc + 4 B/vertex",
     "histocore": "B_HistoCore = B_min + 4(A+n) (histogram build) + 4 B per SumHisto slot "
                  "+ 8 B per arc scanned by UpdateHisto + 8 B per neighbour updated",
@@ -416,8 +416,8 @@ def method_bytes(algo: str, st: dict, n: int, arcs: int, w_r: int) -> int:
     """Algorithmic bytes of one launch (the per-graph figures of the
     measurement plan), from the launch's own counters."""
     b_min = w_r * (n + 1) + 8 * arcs + 4 * n
-    if algo == "peelone":
-        return b_min + 4 * st["atomics"] + 4 * st["scanned"]
+    if algo == "peelone":   # successful decrements only: the others are overhead
+        return b_min + 4 * (st["atomics"] - st["extra"]) + 4 * st["scanned"]
     # HistoCore: InitHisto scans every arc once (counted in st["arcs"] too);
     # each updated neighbour costs two slot edits (counted in st["atomics"])
     update_arcs = st["arcs"] - arcs

@@ -248,3 +248,34 @@ def test_recomputation_fallback(pico, policy):
         # and so is the last, 5x larger than any earlier one
         assert kinds[0] == pico.PICO_DYN_MAINTAINED and kinds[1] == pico.PICO_DYN_MAINTAINED
         assert kinds[4] == pico.PICO_DYN_MAINTAINED
+
+
+def test_hub_row_longer_than_two_pieces(pico):
+    """A hub of degree 10,300 (its row spans three 4,096-arc pieces of the
+    CSR rebuild, and many 1,024-arc steps of a piece) loses arcs spread over
+    all of its row and gains new ones in the same batches; the coreness and
+    the rebuilt arc set must match the oracle after every batch."""
+    rng = np.random.default_rng(63)
+    leaves = 10300
+    n = leaves + 1 + 300
+    edges = {(0, v) for v in range(1, leaves + 1)}
+    for _ in range(3000):   # a denser part among the leaves and some outside vertices
+        a, b = (int(x) for x in rng.integers(1, n, size=2))
+        if a != b:
+            edges.add((min(a, b), max(a, b)))
+    g = gg.from_edge_list(sorted(edges), n)
+    dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=2 * len(edges) + 40000)
+    dg.set_policy(pico.PICO_DYN_MAINTAIN)
+    check(pico, dg, n, edges)
+    for step in range(3):
+        hub = sorted(e for e in edges if e[0] == 0)
+        dele = sorted(set(hub[step::37][:300] + hub[-(5 + step):]))   # the whole row and its end
+        ins = set()
+        while len(ins) < 400:
+            a, b = (int(x) for x in rng.integers(0, n, size=2))
+            e = (min(a, b), max(a, b))
+            if a != b and e not in edges and e not in ins:
+                ins.add(e)
+        dg.update(insert=sorted(ins), delete=dele)
+        edges = (edges - set(dele)) | ins
+        check(pico, dg, n, edges)
