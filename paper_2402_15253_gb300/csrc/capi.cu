@@ -1,5 +1,6 @@
 // The C ABI declared in include/pico.h: argument checks, per-device state,
 // stream-ordered scratch allocation and dispatch to the persistent kernels.
+#include <algorithm>
 #include <cstddef>
 #include <cstdlib>
 #include <cstring>
@@ -60,6 +61,27 @@ int device_state(DeviceState **out)
         d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk, pico::kClusterLog2};
         d.cfg.batched_threads = pico::kThreads;
         d.cfg.peel_async = env_ll("PICO_PEEL_WAVES", 0) == 0;
+        // With PICO_L2_PERSIST=1, the L2 set-aside for persisting lines (a
+        // limit of this process's context) is raised to the device maximum,
+        // and the PeelOne launches mark their residual degrees persisting and
+        // return them to normal status when they end. Off by default: the
+        // set-aside slows HistoCore in the same process more than it helps
+        // PeelOne.
+        d.cfg.l2_window = 0;
+        if (env_ll("PICO_L2_PERSIST", 0) == 1) {
+            int mx = 0, mw = 0;
+            size_t cur = 0;
+            if (cudaDeviceGetAttribute(&mx, cudaDevAttrMaxPersistingL2CacheSize, dev) ==
+                    cudaSuccess &&
+                cudaDeviceGetAttribute(&mw, cudaDevAttrMaxAccessPolicyWindowSize, dev) ==
+                    cudaSuccess &&
+                mx > 0 && mw > 0 && cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
+                if (cur < (size_t)mx && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, mx) == cudaSuccess)
+                    cur = mx;
+                d.cfg.l2_window = std::min<size_t>(cur, (size_t)mw);
+            }
+            cudaGetLastError();
+        }
         if (cudaMalloc(&d.last, sizeof(pico::LastResult)) != cudaSuccess) {
             cudaGetLastError();
             return PICO_ERR_OOM;

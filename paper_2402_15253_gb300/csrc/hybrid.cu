@@ -13,6 +13,8 @@
 // faster exactly on the skewed graphs (d_max >= 64 d_avg) that are small
 // against their skew: m^2 <= 2^14 d_max n, i.e. m <= 2^14 d_max / d_avg.
 // Results never depend on the choice; pico_get_stats reports the method used.
+#include <algorithm>
+
 #include "histocore.cuh"
 #include "peelone.cuh"
 #include "pico.h"
@@ -142,9 +144,13 @@ int launch_hybrid(const Off *rp, const int *ci, long long n, long long m, int *c
     if (cudaMemsetAsync(pp.ctl, 0, sizeof(Ctrl), stream) != cudaSuccess) return -3;
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&pp, &hp, &last, &limit};
-    if (launch_cooperative((const void *)hybrid_kernel<Off>, dim3(ctas),
-                                    dim3(kThreads), args, 0, stream) != cudaSuccess)
+    // PeelOne's residual degrees stay in L2 (when HistoCore runs, the window
+    // covers part of its scratch instead, which is harmless)
+    const size_t win = pp.work ? std::min<size_t>((size_t)n * sizeof(int), cfg.l2_window) : 0;
+    if (launch_cooperative((const void *)hybrid_kernel<Off>, dim3(ctas), dim3(kThreads), args, 0,
+                           stream, pp.work, win) != cudaSuccess)
         return -3;
+    if (win > 0 && l2_release(pp.work, win, stream) != cudaSuccess) return -3;
     return 0;
 }
 

@@ -2,6 +2,8 @@
 // kernel: the algorithm body is peel::run_async (peelone.cuh) over the whole
 // grid, or peel::run (a grid barrier per frontier wave) when asynchronous
 // levels are switched off.
+#include <algorithm>
+
 #include "peelone.cuh"
 #include "pico.h"
 #include "pico_launch.h"
@@ -42,7 +44,42 @@ __global__ void __launch_bounds__(kThreads, 2)
                  st, kStCount);
 }
 
+// Reads a range (16 bytes a thread per step); the values are not used.
+__global__ void __launch_bounds__(256) touch_kernel(const int4 *p, size_t count, int *sink)
+{
+    int acc = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int4 v = __ldcg(p + i);
+        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x7fffffff && sink) *sink = acc;   // keeps the loads
+}
+
 }  // namespace
+
+cudaError_t l2_release(const void *p, size_t bytes, cudaStream_t stream)
+{
+    const size_t count = bytes / sizeof(int4);
+    if (!p || count == 0) return cudaSuccess;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)std::min<size_t>((count + 255) / 256, 1024));
+    lc.blockDim = dim3(256);
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(p);
+    attr[0].val.accessPolicyWindow.num_bytes = count * sizeof(int4);
+    attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyNormal;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const int4 *q = static_cast<const int4 *>(p);
+    int *sink = nullptr;
+    void *args[] = {&q, (void *)&count, &sink};
+    return cudaLaunchKernelExC(&lc, (const void *)touch_kernel, args);
+}
 
 size_t chunk_capacity(long long m) { return peel::chunk_list_capacity(m); }
 
@@ -90,8 +127,12 @@ int launch_peelone(const Off *rp, const int *ci, long long n, long long m, int *
     dim3 grid(ctas), block(kThreads);
     unsigned long long limit = cfg.limit_ns;
     void *args[] = {&p, &last, &limit};
-    if (launch_cooperative(fns[async][mode], grid, block, args, 0, stream) != cudaSuccess)
+    // the residual degrees (the target of every decrement) stay in L2
+    const size_t win = async ? std::min<size_t>((size_t)n * sizeof(int), cfg.l2_window) : 0;
+    if (launch_cooperative(fns[async][mode], grid, block, args, 0, stream, p.work, win) !=
+        cudaSuccess)
         return -3;
+    if (win > 0 && l2_release(p.work, win, stream) != cudaSuccess) return -3;
     return 0;
 }
 

@@ -21,26 +21,45 @@ struct LaunchCfg {
     Tuning tn;                     // degree-class work assignment
     int batched_threads;           // threads per CTA of the batched kernel (256 or 512)
     bool peel_async = false;       // single-graph PeelOne: asynchronous levels (run_async)
+    size_t l2_window = 0;          // largest L2 access-policy window to mark persisting (0: none)
 };
 
 // Launches a persistent kernel whose CTAs must all be resident at once (its
 // grid barrier waits for every CTA): a cooperative launch, made through
 // cudaLaunchKernelExC so that a stream capture can record it in a CUDA graph.
+// With win_bytes > 0, the launch also marks [win, win + win_bytes) as
+// persisting in L2 (an access-policy window; the lines keep that status after
+// the kernel until l2_release).
 inline cudaError_t launch_cooperative(const void *fn, dim3 grid, dim3 block, void **args,
-                                      size_t smem, cudaStream_t stream)
+                                      size_t smem, cudaStream_t stream,
+                                      const void *win = nullptr, size_t win_bytes = 0)
 {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = grid;
     lc.blockDim = block;
     lc.dynamicSmemBytes = smem;
     lc.stream = stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
+    if (win && win_bytes > 0) {
+        attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[1].val.accessPolicyWindow.base_ptr = const_cast<void *>(win);
+        attr[1].val.accessPolicyWindow.num_bytes = win_bytes;
+        attr[1].val.accessPolicyWindow.hitRatio = 1.0f;
+        attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        lc.numAttrs = 2;
+    }
     return cudaLaunchKernelExC(&lc, fn, args);
 }
+
+// Returns the lines of [p, p + bytes) that a launch marked persisting to
+// normal status (a read of the range under a window with the normal
+// property), so that they stop taking L2 from later kernels. Stream-ordered.
+cudaError_t l2_release(const void *p, size_t bytes, cudaStream_t stream);
 
 // Sub-buffer carving of a scratch allocation (256-byte aligned pieces).
 struct Carver {
