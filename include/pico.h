@@ -343,8 +343,10 @@ void pico_dyn_destroy(pico_dyn *d);
  * computation's. The prediction scales the device time (measured with
  * events) that the deletion step and the insertion passes took in the last
  * batches that ran them by the ratio of edge counts, and is made only when
- * those batches were within a factor of two of this one in size; otherwise
- * the batch is maintained (and measured). PICO_DYN_MAINTAIN always
+ * those batches were within a factor of two of this one in size (otherwise
+ * the batch is maintained, and measured); insertion passes that follow
+ * deletions add one count of neighbour estimates over all arcs, timed when
+ * the state was created. PICO_DYN_MAINTAIN always
  * maintains, PICO_DYN_RECOMPUTE always recomputes. The result is the same
  * coreness either way. pico_dyn_last_update_kind reports what the last update
  * did (PICO_DYN_MAINTAINED or PICO_DYN_RECOMPUTED; after a recomputation

@@ -953,6 +953,7 @@ struct pico_dyn {
     // each maintenance step (deletions, insertions; size 0: none yet).
     double full_ms = 0, del_ms = 0, ins_ms = 0;
     long long del_k = 0, ins_k = 0;
+    double cd_ms = 0;   // one count of cd over all arcs (insertion passes after deletions)
     int policy = PICO_DYN_AUTO;
     int last_kind = PICO_DYN_MAINTAINED;
 };
@@ -1097,7 +1098,10 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
     // cd for the first insertion batch: one count over all arcs
     void *ws = nullptr;
     ok = ok && cudaMallocAsync(&ws, pico::dyn::maint_ws_bytes(n, m), s) == cudaSuccess;
+    EventTimer count;
+    count.start(s);
     ok = ok && launch_maint(d, d->rp[0], d->ci[0], m, nullptr, 0, false, true, ws, s, cfg, last);
+    count.stop(s);
     if (ws) cudaFreeAsync(ws, s);
     ok = ok && sync_status(s) == PICO_OK && pico_last_device_status(stream) == PICO_OK;
     if (!ok) {
@@ -1107,6 +1111,7 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
     }
     d->cd_valid = true;
     d->full_ms = full.ms();
+    d->cd_ms = std::max(0.0, count.ms());
     return d;
 }
 
@@ -1220,13 +1225,17 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     // is predicted from the last batch that ran it, scaled by the edge
     // counts, only when the sizes are within a factor of two (a step's cost
     // is not linear over a wider range); otherwise the batch is maintained
-    // and measured.
+    // and measured. Insertion passes that must first recount cd (after
+    // deletions, or when cd is stale) add one count over all arcs, timed
+    // when the state was created.
+    const bool cd_recount = n_ins > 0 && !(cd_was_valid && n_del == 0);
     bool recompute = d->policy == PICO_DYN_RECOMPUTE;
     if (d->policy == PICO_DYN_AUTO && d->full_ms > 0) {
         auto near = [](long long k, long long k0) { return k0 > 0 && 2 * k >= k0 && k <= 2 * k0; };
         const bool known = (n_del == 0 || near(n_del, d->del_k)) && (n_ins == 0 || near(n_ins, d->ins_k));
         const double pred = (n_del ? d->del_ms * (double)n_del / (double)std::max(1ll, d->del_k) : 0.0) +
-                            (n_ins ? d->ins_ms * (double)n_ins / (double)std::max(1ll, d->ins_k) : 0.0);
+                            (n_ins ? d->ins_ms * (double)n_ins / (double)std::max(1ll, d->ins_k) : 0.0) +
+                            (cd_recount ? d->cd_ms : 0.0);
         recompute = known && pred > d->full_ms;
     }
     if (recompute) {
@@ -1273,8 +1282,8 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
             d->del_ms = a;
             d->del_k = n_del;
         }
-        if (n_ins > 0 && b > 0) {
-            d->ins_ms = b;
+        if (n_ins > 0 && b > 0) {   // the passes alone, without the recount of cd
+            d->ins_ms = std::max(0.1 * b, b - (cd_recount ? d->cd_ms : 0.0));
             d->ins_k = n_ins;
         }
     }
