@@ -990,8 +990,10 @@ def main():
                                             {a: statistics.median(v) for a, v in per.items()},
                                             stream)
     if rank == 0 and not args.no_maintenance:
+        # the updates run every kind of kernel (HistoCore for deletions, the
+        # insertion passes, or a recomputation): the default tuning
         line["maintenance"] = bench_maintenance(
-            pico, g, stream, update_tuning=tuned["histocore"],
+            pico, g, stream, update_tuning=autotune_default(),
             recompute_tuning=tuned[line["auto"]["method"]] if rank == 0 else None)
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)

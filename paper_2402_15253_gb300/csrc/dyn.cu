@@ -327,8 +327,21 @@ __global__ void __launch_bounds__(512) bulk_copy_kernel(const int *ci, long long
         const long long ns = i + 1 < nT ? seg_start[i + 1] : LLONG_MAX;
         if (c0 >= se && c1 <= ns) {   // no touched arc in the step
             const long long sh = i >= 0 ? shift[i] : 0;
-#pragma unroll 4
-            for (long long e = c0 + lane; e < c1; e += 32) new_ci[e + sh] = ci[e];
+            // all loads of a batch of 8 before its stores (the arrays may
+            // alias as far as the compiler knows): 8 loads in flight a lane
+            for (long long e0 = c0 + lane; e0 < c1; e0 += 8 * 32) {
+                int x[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const long long e = e0 + 32 * j;
+                    x[j] = e < c1 ? __ldcs(ci + e) : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const long long e = e0 + 32 * j;
+                    if (e < c1) __stcs(new_ci + e + sh, x[j]);
+                }
+            }
             continue;
         }
         long long t = i;
@@ -954,6 +967,13 @@ struct pico_dyn {
     double full_ms = 0, del_ms = 0, ins_ms = 0;
     long long del_k = 0, ins_k = 0;
     double cd_ms = 0;   // one count of cd over all arcs (insertion passes after deletions)
+    // scratch of the coreness steps (deletions, insertion passes, a recomputation),
+    // sized for the arc capacity and kept for the state's lifetime
+    void *ws2 = nullptr;
+    size_t ws2_bytes = 0;
+    // scratch of the CSR rebuild (grown to the largest batch seen)
+    void *ws1 = nullptr;
+    size_t ws1_bytes = 0;
     int policy = PICO_DYN_AUTO;
     int last_kind = PICO_DYN_MAINTAINED;
 };
@@ -1085,6 +1105,10 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
     }
     ok = ok && cudaMalloc(&d->core, (size_t)n * sizeof(int)) == cudaSuccess;
     ok = ok && cudaMalloc(&d->cd, (size_t)n * sizeof(int)) == cudaSuccess;
+    d->ws2_bytes = std::max({pico::histocore_ws_bytes(n, capacity_arcs),
+                             pico::dyn::maint_ws_bytes(n, capacity_arcs),
+                             pico::hybrid_ws_bytes(n, capacity_arcs)});
+    ok = ok && cudaMalloc(&d->ws2, d->ws2_bytes) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(d->rp[0], row_ptr, (size_t)(n + 1) * sizeof(long long),
                                cudaMemcpyDeviceToDevice, s) == cudaSuccess;
     ok = ok && (m == 0 || cudaMemcpyAsync(d->ci[0], col_idx, (size_t)m * sizeof(int),
@@ -1096,13 +1120,11 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
                    PICO_OK;
     full.stop(s);
     // cd for the first insertion batch: one count over all arcs
-    void *ws = nullptr;
-    ok = ok && cudaMallocAsync(&ws, pico::dyn::maint_ws_bytes(n, m), s) == cudaSuccess;
     EventTimer count;
     count.start(s);
-    ok = ok && launch_maint(d, d->rp[0], d->ci[0], m, nullptr, 0, false, true, ws, s, cfg, last);
+    ok = ok && launch_maint(d, d->rp[0], d->ci[0], m, nullptr, 0, false, true, d->ws2, s, cfg,
+                            last);
     count.stop(s);
-    if (ws) cudaFreeAsync(ws, s);
     ok = ok && sync_status(s) == PICO_OK && pico_last_device_status(stream) == PICO_OK;
     if (!ok) {
         cudaGetLastError();
@@ -1154,13 +1176,21 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     c0.take<int>(nt_cap);                // the long ones
     for (int i = 0; i < 3; ++i) c0.take<long long>(nt_cap);   // their arc ranges, shifts
     const size_t pre_bytes = c0.size();
-    const size_t bytes = pre_bytes + std::max(pico::histocore_ws_bytes(n, m_new),
-                                              pico::dyn::maint_ws_bytes(n, m_new));
-    void *ws = nullptr;
-    if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
-        cudaGetLastError();
-        return PICO_ERR_OOM;
+    if (pre_bytes > d->ws1_bytes) {   // grow the rebuild's scratch (kept for later batches)
+        if (d->ws1) {
+            cudaStreamSynchronize(s);
+            cudaFree(d->ws1);
+        }
+        d->ws1 = nullptr;
+        d->ws1_bytes = 0;
+        if (cudaMalloc(&d->ws1, pre_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            d->ws1 = nullptr;
+            return PICO_ERR_OOM;
+        }
+        d->ws1_bytes = pre_bytes;
     }
+    void *ws = d->ws1;
     Carver c(ws);
     int *ins_cnt = c.take<int>(n), *del_cnt = c.take<int>(n), *cursor = c.take<int>(n);
     unsigned char *touched = c.take<unsigned char>(n + 4);
@@ -1173,7 +1203,7 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     int *T = c.take<int>(nt_cap), *big = c.take<int>(nt_cap);
     long long *seg_start = c.take<long long>(nt_cap), *seg_end = c.take<long long>(nt_cap);
     long long *shift = c.take<long long>(nt_cap);
-    void *ws2 = static_cast<char *>(ws) + pre_bytes;
+    void *ws2 = d->ws2;
     int *nbig = flags, *err = flags + 1;
     const int G = cfg.sms * 4;
     auto scan = [&](long long *arr, pico::Ctrl *ctl) {   // in-place scan of arr[1..n]
@@ -1212,7 +1242,6 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     ok = ok && cudaMemcpy(&m_chk, nrp + n, sizeof(long long), cudaMemcpyDeviceToHost) == cudaSuccess;
     if (!ok || herr != 0 || m_chk != m_new) {
         cudaGetLastError();
-        cudaFreeAsync(ws, s);
         return !ok ? PICO_ERR_CUDA : PICO_ERR_BAD_GRAPH;   // the state is unchanged
     }
     // the graph is consistent: switch to it and bring the coreness up to date
@@ -1239,13 +1268,21 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
         recompute = known && pred > d->full_ms;
     }
     if (recompute) {
-        cudaFreeAsync(ws, s);
         EventTimer full;
         full.start(s);
-        rc = pico_coreness_i64(reinterpret_cast<const int64_t *>(nrp), nci, n, m_new, d->core,
-                               PICO_ALGO_AUTO, stream);
+        if (m_new > 0)   // PICO_ALGO_AUTO on the state's scratch
+            rc = pico::launch_hybrid<long long>(nrp, nci, n, m_new, d->core, ws2, last, s, cfg) == 0
+                     ? PICO_OK
+                     : PICO_ERR_CUDA;
+        else
+            rc = cudaMemsetAsync(d->core, 0, (size_t)n * sizeof(int), s) == cudaSuccess
+                     ? PICO_OK
+                     : PICO_ERR_CUDA;
         full.stop(s);
-        if (rc != PICO_OK) return rc;
+        if (rc != PICO_OK) {
+            cudaGetLastError();
+            return rc;
+        }
         if (sync_status(s) != PICO_OK) return PICO_ERR_CUDA;
         const double t = full.ms();
         if (t > 0) d->full_ms = t;
@@ -1267,7 +1304,6 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
         ok = launch_maint(d, nrp, nci, m_new, ins, n_ins, cd_was_valid && n_del == 0, false, ws2,
                           s, cfg, last);
     tins.stop(s);
-    cudaFreeAsync(ws, s);
     if (!ok) {
         cudaGetLastError();
         return PICO_ERR_CUDA;
@@ -1348,6 +1384,8 @@ void pico_dyn_destroy(pico_dyn *d)
     }
     if (d->core) cudaFree(d->core);
     if (d->cd) cudaFree(d->cd);
+    if (d->ws2) cudaFree(d->ws2);
+    if (d->ws1) cudaFree(d->ws1);
     cudaGetLastError();
     delete d;
 }
