@@ -84,3 +84,33 @@ def test_request_larger_than_budget_is_rejected(pico):
     srv = pico.pico_server_create(1 << 20, 0, 2, 8, 0)
     assert pico.pico_server_submit(srv, rp, ci, g.n, g.arcs, out, 0) == pico.PICO_ERR_OOM
     assert pico.pico_server_destroy(srv) == 0
+
+
+def test_served_workload_mix_with_scale20_outliers(pico):
+    """The served workload's shape: request graphs from the batch size
+    distribution (100..200,000 vertices, half ER, half R-MAT) with R-MAT scale
+    20 outliers (about 16.6 M arcs each) among them, Poisson arrivals, a
+    40 GB admission budget; every result must be the oracle's."""
+    import math
+    specs = gg.batch_specs(60, 94)
+    graphs = [gg.spec_graph(s) for s in specs]
+    for i, pos in enumerate((7, 23, 41)):
+        graphs.insert(pos, gg.rmat_graph(20, 16, gg.SEED_BASE + 50 + i))
+    reqs = []
+    for g in graphs:
+        rp = g.row_ptr.to(torch.int32).pin_memory()
+        ci = g.col_idx.pin_memory() if g.arcs else torch.zeros(1, dtype=torch.int32).pin_memory()
+        out = torch.full((max(g.n, 1),), -1, dtype=torch.int32).pin_memory()
+        reqs.append((g, rp, ci, out))
+    srv = pico.pico_server_create(40 << 30, 0, 4, 512, 0)
+    assert srv
+    t0 = pico.pico_clock_ns() + 1_000_000
+    t = 0.0
+    for i, (g, rp, ci, out) in enumerate(reqs):
+        t += -math.log(1.0 - gg.unit_int(94, 7, i)) / 4000.0   # about 4,000 requests/s
+        assert pico.pico_server_submit(srv, rp, ci, g.n, g.arcs, out, t0 + int(t * 1e9)) >= 0
+    assert pico.pico_server_drain(srv) == 0
+    assert pico.pico_server_destroy(srv) == 0
+    for g, _, _, out in reqs:
+        want = oracle.bz_coreness(g.row_ptr.numpy(), g.col_idx.numpy())
+        assert np.array_equal(out[:g.n].numpy(), want)
