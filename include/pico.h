@@ -400,7 +400,11 @@ int pico_dyn_last_update_kind(pico_dyn *d);
  *
  * pico_coreness_partitioned runs the whole computation on the current device
  * with `parts` partitions of equal vertex ranges, moving the records between
- * them itself; *rounds (if not NULL) receives the number of rounds. It
+ * them itself; *rounds (if not NULL) receives the number of rounds. Since
+ * every partition can read the whole graph there, a round whose changed
+ * vertices hold less than half the arcs divided by the partitions is pushed
+ * (the changed vertices walk their arcs; each partition applies the edits on
+ * its rows) instead of pulled; the result and the rounds are the same. It
  * synchronises `stream`. row_ptr is int64 (n + 1), col_idx has m entries.
  */
 typedef struct pico_part pico_part;

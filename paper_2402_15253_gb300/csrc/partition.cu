@@ -22,7 +22,12 @@
 //            one decrement took it from K to K - 1); the array is cleared.
 // No kernel waits on another: each phase is an ordinary launch that ends,
 // and the exchange sits between launches, so partitions can live on other
-// devices (or processes) with the same calls.
+// devices (or processes) with the same calls. A partition reads only its own
+// rows of the graph. The single-device driver (pico_coreness_partitioned),
+// where every partition can read the whole graph, also pushes: in a round
+// whose changed vertices hold few arcs, those vertices walk their own arcs
+// and each partition applies the edits that fall on its rows (the same
+// edits as pulled, reached from the other end of each arc).
 //
 // Rows are addressed by local index i (vertex lo + i); their adjacency is
 // col_idx[row_ptr[lo + i] ..] with global neighbour ids; the histogram of a
@@ -45,6 +50,7 @@ struct Counters {
     unsigned nib;          // chunk entries of the large rows
     int ymax;              // INT_MAX - smallest new estimate of the round (atomicMax)
     int err;
+    unsigned long long vol;   // arcs of the round's changed vertices
 };
 
 struct Arrays {
@@ -153,6 +159,7 @@ __device__ __forceinline__ void apply_sum(const Arrays &a, int i, int K, int h, 
     a.rec[3 * pos + 1] = K;
     a.rec[3 * pos + 2] = h;
     atomicMax(&a.cnt->ymax, INT_MAX - h);
+    atomicAdd(&a.cnt->vol, (unsigned long long)(a.lrp[i + 1] - a.lrp[i]));
 }
 
 __global__ void __launch_bounds__(kBlock) sum_kernel(Arrays a, int par, unsigned nv)
@@ -286,6 +293,110 @@ __global__ void __launch_bounds__(kBlock) collect_kernel(Arrays a, int np_par)
     }
 }
 
+// Push form of UpdateHisto for the single-device driver, where every
+// partition can read the whole CSR: the round's changed vertices (listed
+// once for all partitions: small ones, chunks of large ones) walk their own
+// arcs, and each partition applies the edits that fall on its rows. It
+// applies the same multiset of edits as the pull form (arc (w, u) pushed is
+// arc (u, w) pulled) and marks the same rows; it scans the changed vertices'
+// arcs once per partition instead of every arc of the partition's rows.
+struct PushLists {
+    int *small;        // changed vertices of degree <= small_deg
+    int2 *big;         // (vertex, chunk) entries of the larger ones
+    unsigned *count;   // [0] small, [1] big
+    unsigned small_cap, big_cap;
+    int *err;
+};
+
+__global__ void __launch_bounds__(kBlock) push_lists_kernel(const long long *rp, long long n,
+                                                            const int *rec, long long count,
+                                                            PushLists l, Tuning tn)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < count; b += stride) {
+        const long long r = b + threadIdx.x;
+        int w = -1;
+        long long d = 0;
+        if (r < count) {
+            w = rec[3 * r];
+            if (w >= 0 && w < n) d = rp[w + 1] - rp[w];
+            else w = -1;
+        }
+        const bool small = w >= 0 && d > 0 && d <= tn.small_deg;
+        const unsigned pos = warp_push(&l.count[0], small);
+        if (small) {
+            if (pos < l.small_cap) l.small[pos] = w;
+            else *l.err = 1;
+        }
+        const unsigned lane = threadIdx.x & 31;
+        unsigned m = __ballot_sync(kFull, w >= 0 && d > tn.small_deg);
+        while (m) {   // the warp writes each large vertex's chunk entries
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const int vv = __shfl_sync(kFull, w, src);
+            const long long dd = __shfl_sync(kFull, d, src);
+            const unsigned nch = (unsigned)((dd + tn.chunk - 1) / tn.chunk);
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(&l.count[1], nch);
+            base = __shfl_sync(kFull, base, 0);
+            if ((unsigned long long)base + nch > l.big_cap) {
+                if (lane == 0) *l.err = 1;
+                continue;
+            }
+            for (unsigned c = lane; c < nch; c += 32) l.big[base + c] = make_int2(vv, (int)c);
+        }
+    }
+}
+
+struct PushArc {
+    static constexpr int kArcs = 4;
+    const int2 *mvg;
+    const int *est;
+    const long long *lrp;
+    int *hist;
+    unsigned char *cand;
+    long long lo, np;
+    __device__ __forceinline__ bool item(int w, int &x, int &y)
+    {
+        const int2 r = mvg[w];
+        x = r.x;
+        y = r.y;
+        return x != 0;
+    }
+    __device__ __forceinline__ void arcs(const bool (&valid)[kArcs], const int (&)[kArcs],
+                                         const int (&u)[kArcs], const long long (&)[kArcs],
+                                         const int (&x)[kArcs], const int (&y)[kArcs])
+    {
+        long long i[kArcs];
+        int K[kArcs];
+        long long rs[kArcs];
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            i[j] = (long long)u[j] - lo;
+            const bool mine = valid[j] && i[j] >= 0 && i[j] < np;
+            K[j] = mine ? est[i[j]] : 0;
+            rs[j] = mine ? lrp[i[j]] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kArcs; ++j) {
+            if (K[j] <= y[j]) continue;   // not this partition's row, or no edit (K <= y)
+            red_add(hist + rs[j] + y[j] - 1, 1);
+            red_add(hist + rs[j] + (x[j] < K[j] ? x[j] : K[j]) - 1, -1);
+            if (x[j] >= K[j]) cand[i[j]] = 1;
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kBlock) push_kernel(Arrays a, PushLists l)
+{
+    PushArc f{a.mvg, a.est, a.lrp, a.hist, a.cand, a.lo, a.np};
+    const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned ns = l.count[0] < l.small_cap ? l.count[0] : l.small_cap;
+    const unsigned nb = l.count[1] < l.big_cap ? l.count[1] : l.big_cap;
+    expand(a.rp, a.ci, l.small, ns, l.big, nb, gwarp, nwarps, f, a.tn);
+}
+
 }  // namespace part
 }  // namespace pico
 
@@ -298,30 +409,18 @@ struct pico_part {
     unsigned long long vcnt;   // its size
     long long changed;         // records of the last sum
     int ymin;                  // smallest new estimate of the last sum
+    unsigned long long vol;    // arcs of the vertices of those records
     int grid;
 };
 
 namespace {
 
-int sync_err(pico_part *p, cudaStream_t s)
+// Synchronises the stream and copies the partition's counters to *c; the
+// status of what the partition's kernels found.
+int sync_read(pico_part *p, cudaStream_t s, pico::part::Counters *c)
 {
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return PICO_ERR_CUDA;
-    }
-    pico::part::Counters c;
-    if (cudaMemcpy(&c, p->a.cnt, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) {
-        cudaGetLastError();
-        return PICO_ERR_CUDA;
-    }
-    if (c.err == 1) return PICO_ERR_NOT_CONVERGED;
-    if (c.err) return PICO_ERR_BAD_GRAPH;
-    return PICO_OK;
-}
-
-int read_counters(pico_part *p, pico::part::Counters *c)
-{
-    if (cudaMemcpy(c, p->a.cnt, sizeof *c, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpy(c, p->a.cnt, sizeof *c, cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();
         return PICO_ERR_CUDA;
     }
@@ -405,7 +504,7 @@ pico_part *pico_part_create(const int64_t *row_ptr, const int32_t *col_idx, int6
         ok = cudaGetLastError() == cudaSuccess;
     }
     pico::part::Counters cn{};
-    ok = ok && sync_err(p, s) == PICO_OK && read_counters(p, &cn) == PICO_OK;
+    ok = ok && sync_read(p, s, &cn) == PICO_OK;
     if (!ok) {
         cudaGetLastError();
         cudaFree(p->mem);
@@ -424,7 +523,8 @@ int pico_part_sum(pico_part *p, int64_t *n_changed, int32_t *ymin, pico_stream_t
     // counters of this round: records and their smallest estimate
     pico::part::Counters *cd = p->a.cnt;
     if (cudaMemsetAsync(&cd->changed, 0, sizeof(unsigned), s) != cudaSuccess ||
-        cudaMemsetAsync(&cd->ymax, 0, sizeof(int), s) != cudaSuccess) {
+        cudaMemsetAsync(&cd->ymax, 0, sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(&cd->vol, 0, sizeof(unsigned long long), s) != cudaSuccess) {
         cudaGetLastError();
         return PICO_ERR_CUDA;
     }
@@ -432,14 +532,13 @@ int pico_part_sum(pico_part *p, int64_t *n_changed, int32_t *ymin, pico_stream_t
         pico::part::sum_kernel<<<p->grid, pico::part::kBlock, 0, s>>>(p->a, par, (unsigned)p->vcnt);
         if (cudaGetLastError() != cudaSuccess) return PICO_ERR_CUDA;
     }
-    int rc = sync_err(p, s);
-    if (rc != PICO_OK) return rc;
     pico::part::Counters c{};
-    rc = read_counters(p, &c);
+    const int rc = sync_read(p, s, &c);
     if (rc != PICO_OK) return rc;
     if (c.changed != p->vcnt) return PICO_ERR_BAD_GRAPH;   // Thm. 2: every V_cnt vertex changes
     p->changed = c.changed;
     p->ymin = c.changed ? INT_MAX - c.ymax : INT_MAX;
+    p->vol = c.vol;
     *n_changed = p->changed;
     *ymin = p->ymin;
     return PICO_OK;
@@ -459,8 +558,14 @@ int pico_part_copy_records(pico_part *p, int32_t *dst, pico_stream_t stream)
     return PICO_OK;
 }
 
-int pico_part_apply(pico_part *p, const int32_t *records, int64_t count, int32_t ymin,
-                    int64_t *next_vcnt, pico_stream_t stream)
+}  // extern "C"
+
+namespace {
+// UpdateHisto of one partition for the round's records: pulled into its
+// rows, or (push != nullptr, single device only) pushed from the listed
+// changed vertices.
+int apply_impl(pico_part *p, const int32_t *records, int64_t count, int32_t ymin,
+               int64_t *next_vcnt, pico_stream_t stream, const pico::part::PushLists *push)
 {
     if (!p || count < 0 || (count > 0 && !records) || !next_vcnt) return PICO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -474,22 +579,32 @@ int pico_part_apply(pico_part *p, const int32_t *records, int64_t count, int32_t
         const int g = (int)std::min<long long>(p->grid, (count + pico::part::kBlock - 1) / pico::part::kBlock);
         pico::part::scatter_kernel<<<g, pico::part::kBlock, 0, s>>>(p->a.mvg, p->n, records, count,
                                                                     false, &cd->err);
-        if (p->m_local > 0)
+        if (p->m_local > 0 && push)
+            pico::part::push_kernel<<<p->grid, pico::part::kBlock, 0, s>>>(p->a, *push);
+        else if (p->m_local > 0)
             pico::part::pull_kernel<<<p->grid, pico::part::kBlock, 0, s>>>(p->a, ymin);
         pico::part::collect_kernel<<<p->grid, pico::part::kBlock, 0, s>>>(p->a, np_par);
         pico::part::scatter_kernel<<<g, pico::part::kBlock, 0, s>>>(p->a.mvg, p->n, records, count,
                                                                     true, &cd->err);
         if (cudaGetLastError() != cudaSuccess) return PICO_ERR_CUDA;
     }
-    int rc = sync_err(p, s);
-    if (rc != PICO_OK) return rc;
     pico::part::Counters c{};
-    rc = read_counters(p, &c);
+    const int rc = sync_read(p, s, &c);
     if (rc != PICO_OK) return rc;
     p->par = np_par;
     p->vcnt = c.vcnt[np_par];
     *next_vcnt = (int64_t)p->vcnt;
     return PICO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pico_part_apply(pico_part *p, const int32_t *records, int64_t count, int32_t ymin,
+                    int64_t *next_vcnt, pico_stream_t stream)
+{
+    return apply_impl(p, records, count, ymin, next_vcnt, stream, nullptr);
 }
 
 int pico_part_coreness(pico_part *p, int32_t *out_core, pico_stream_t stream)
@@ -533,9 +648,34 @@ int pico_coreness_partitioned(const int64_t *row_ptr, const int32_t *col_idx, in
         cudaGetLastError();
         rc = PICO_ERR_OOM;
     }
+    // lists of a pushed round's changed vertices, shared by the partitions
+    pico::part::PushLists pl{};
+    void *plmem = nullptr;
+    pico::LaunchCfg cfg;
+    pico::LastResult *last = nullptr;
+    if (rc == PICO_OK) rc = pico::current_device(&cfg, &last);
+    if (rc == PICO_OK) {
+        pico::Carver c(nullptr);
+        c.take<unsigned>(4);
+        c.take<int>(n);
+        c.take<int2>(pico::chunk_capacity(m));
+        if (cudaMalloc(&plmem, c.size()) != cudaSuccess) {
+            cudaGetLastError();
+            rc = PICO_ERR_OOM;
+        } else {
+            pico::Carver d(plmem);
+            pl.count = d.take<unsigned>(4);
+            pl.err = reinterpret_cast<int *>(pl.count + 2);
+            pl.small = d.take<int>(n);
+            pl.small_cap = (unsigned)n;
+            pl.big = d.take<int2>(pico::chunk_capacity(m));
+            pl.big_cap = (unsigned)pico::chunk_capacity(m);
+        }
+    }
     long long r = 0;
     while (rc == PICO_OK) {
         long long total = 0;
+        unsigned long long vol = 0;
         int ymin = INT_MAX;
         for (int q = 0; q < P && rc == PICO_OK; ++q) {   // SumHisto in every partition
             int64_t c = 0;
@@ -550,6 +690,7 @@ int pico_coreness_partitioned(const int64_t *row_ptr, const int32_t *col_idx, in
                 rc = PICO_ERR_CUDA;
             }
             total += c;
+            vol += ps[q]->vol;
             ymin = std::min(ymin, (int)y);
         }
         if (rc != PICO_OK || total == 0) break;
@@ -558,9 +699,37 @@ int pico_coreness_partitioned(const int64_t *row_ptr, const int32_t *col_idx, in
             rc = PICO_ERR_NOT_CONVERGED;
             break;
         }
+        // Push when every partition scanning the changed vertices' arcs costs
+        // less than half of pulling every arc (the measured crossover of the
+        // single-graph kernel is near half the arcs).
+        const bool push = (unsigned long long)P * vol * 2 < (unsigned long long)m;
+        if (push) {
+            if (cudaMemsetAsync(pl.count, 0, 4 * sizeof(unsigned), s) != cudaSuccess) {
+                cudaGetLastError();
+                rc = PICO_ERR_CUDA;
+                break;
+            }
+            const int g = (int)std::min<long long>(cfg.sms * 4, (total + pico::part::kBlock - 1) /
+                                                                    pico::part::kBlock);
+            pico::part::push_lists_kernel<<<g, pico::part::kBlock, 0, s>>>(
+                reinterpret_cast<const long long *>(row_ptr), n, all, total, pl, cfg.tn);
+            if (cudaGetLastError() != cudaSuccess) {
+                rc = PICO_ERR_CUDA;
+                break;
+            }
+        }
         for (int q = 0; q < P && rc == PICO_OK; ++q) {   // UpdateHisto in every partition
             int64_t next = 0;
-            rc = pico_part_apply(ps[q], all, total, ymin, &next, stream);
+            rc = apply_impl(ps[q], all, total, ymin, &next, stream, push ? &pl : nullptr);
+        }
+        if (rc == PICO_OK && push) {
+            int perr = 0;
+            if (cudaMemcpy(&perr, pl.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cudaGetLastError();
+                rc = PICO_ERR_CUDA;
+            } else if (perr) {
+                rc = PICO_ERR_NOT_CONVERGED;
+            }
         }
     }
     for (int q = 0; q < P && rc == PICO_OK; ++q)
@@ -570,6 +739,7 @@ int pico_coreness_partitioned(const int64_t *row_ptr, const int32_t *col_idx, in
         rc = PICO_ERR_CUDA;
     }
     cudaFree(all);
+    cudaFree(plmem);
     for (pico_part *p : ps) pico_part_destroy(p);
     if (rounds) *rounds = r;
     return rc;
