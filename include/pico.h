@@ -377,7 +377,8 @@ int pico_dyn_last_update_kind(pico_dyn *d);
  * initial V_cnt; it synchronises `stream` and returns NULL on invalid
  * arguments (0 <= lo < hi <= n required) or failure. The partition owns its
  * device memory (estimates, histograms, lists, and an n-entry {old, new}
- * array) until pico_part_destroy.
+ * array), taken from the stream-ordered allocator on `stream`;
+ * pico_part_destroy releases it on that same stream, which must still exist.
  *
  * pico_part_sum runs SumHisto over the partition's V_cnt and reports the
  * number of records of the round (*n_changed; 0 when its V_cnt was empty)

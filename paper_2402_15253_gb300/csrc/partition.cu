@@ -404,7 +404,8 @@ struct pico_part {
     int device;
     long long n, lo, hi, m_local;
     pico::part::Arrays a;
-    void *mem;
+    void *mem;                 // from the stream-ordered pool, released on `stream`
+    cudaStream_t stream;
     int par;                   // parity of the current V_cnt
     unsigned long long vcnt;   // its size
     long long changed;         // records of the last sum
@@ -468,7 +469,8 @@ pico_part *pico_part_create(const int64_t *row_ptr, const int32_t *col_idx, int6
     c0.take<int>(3 * np);
     c0.take<int2>(n);
     c0.take<int2>(ib_cap);
-    if (cudaMalloc(&p->mem, c0.size()) != cudaSuccess) {
+    p->stream = s;
+    if (cudaMallocAsync(&p->mem, c0.size(), s) != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return nullptr;
@@ -507,7 +509,7 @@ pico_part *pico_part_create(const int64_t *row_ptr, const int32_t *col_idx, int6
     ok = ok && sync_read(p, s, &cn) == PICO_OK;
     if (!ok) {
         cudaGetLastError();
-        cudaFree(p->mem);
+        cudaFreeAsync(p->mem, s);
         delete p;
         return nullptr;
     }
@@ -621,7 +623,8 @@ int pico_part_coreness(pico_part *p, int32_t *out_core, pico_stream_t stream)
 void pico_part_destroy(pico_part *p)
 {
     if (!p) return;
-    cudaFree(p->mem);
+    cudaFreeAsync(p->mem, p->stream);
+    cudaGetLastError();
     delete p;
 }
 
@@ -644,7 +647,7 @@ int pico_coreness_partitioned(const int64_t *row_ptr, const int32_t *col_idx, in
         if (!ps[q]) rc = PICO_ERR_OOM;
     }
     int *all = nullptr;   // every partition's records of a round, in partition order
-    if (rc == PICO_OK && cudaMalloc(&all, (size_t)3 * n * sizeof(int) + 16) != cudaSuccess) {
+    if (rc == PICO_OK && cudaMallocAsync(&all, (size_t)3 * n * sizeof(int) + 16, s) != cudaSuccess) {
         cudaGetLastError();
         rc = PICO_ERR_OOM;
     }
@@ -659,7 +662,7 @@ int pico_coreness_partitioned(const int64_t *row_ptr, const int32_t *col_idx, in
         c.take<unsigned>(4);
         c.take<int>(n);
         c.take<int2>(pico::chunk_capacity(m));
-        if (cudaMalloc(&plmem, c.size()) != cudaSuccess) {
+        if (cudaMallocAsync(&plmem, c.size(), s) != cudaSuccess) {
             cudaGetLastError();
             rc = PICO_ERR_OOM;
         } else {
@@ -738,8 +741,9 @@ int pico_coreness_partitioned(const int64_t *row_ptr, const int32_t *col_idx, in
         cudaGetLastError();
         rc = PICO_ERR_CUDA;
     }
-    cudaFree(all);
-    cudaFree(plmem);
+    if (all) cudaFreeAsync(all, s);
+    if (plmem) cudaFreeAsync(plmem, s);
+    cudaGetLastError();
     for (pico_part *p : ps) pico_part_destroy(p);
     if (rounds) *rounds = r;
     return rc;
