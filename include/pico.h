@@ -361,6 +361,16 @@ int pico_dyn_set_policy(pico_dyn *d, int policy);
 int pico_dyn_last_update_kind(pico_dyn *d);
 
 /*
+ * Device time (CUDA events, milliseconds) of the last successful
+ * pico_dyn_update, split into the CSR rebuild (counts, scans, copies, the
+ * batch's arcs) and the coreness step (deletions plus insertion passes, or
+ * the recomputation). Both are -1 before the first update; the update has
+ * synchronised the stream, so reading them waits for nothing. Returns
+ * PICO_ERR_INVALID_ARG on a null argument. (No counterpart in the paper.)
+ */
+int pico_dyn_last_update_times(pico_dyn *d, double *rebuild_ms, double *coreness_ms);
+
+/*
  * Partitioned HistoCore: Alg. 6 over a graph whose vertices are split into
  * contiguous ranges, each held by one partition (Index2core's fit to a
  * distributed setting, Sec. VI; multi-GPU processing is future work in Sec.

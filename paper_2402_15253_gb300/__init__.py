@@ -145,6 +145,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_dyn_set_policy.restype = i32
     L.pico_dyn_last_update_kind.argtypes = [vp]
     L.pico_dyn_last_update_kind.restype = i32
+    L.pico_dyn_last_update_times.argtypes = [vp, vp, vp]
+    L.pico_dyn_last_update_times.restype = i32
     L.pico_set_histo_update.argtypes = [i32, i32]
     L.pico_set_histo_update.restype = i32
     L.pico_get_histo_update.argtypes = [vp, vp]
@@ -452,6 +454,15 @@ def pico_dyn_last_update_kind(d) -> int:
     return load().pico_dyn_last_update_kind(d)
 
 
+def pico_dyn_last_update_times(d) -> tuple:
+    """(rebuild ms, coreness-step ms) of the last update (-1 before the first)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = load().pico_dyn_last_update_times(d, ctypes.byref(a), ctypes.byref(b))
+    if rc != PICO_OK:
+        raise PicoError(rc, "pico_dyn_last_update_times")
+    return a.value, b.value
+
+
 def pico_dyn_destroy(d) -> None:
     load().pico_dyn_destroy(d)
 
@@ -499,6 +510,11 @@ class DynamicGraph:
     def last_update_kind(self) -> int:
         """PICO_DYN_MAINTAINED or PICO_DYN_RECOMPUTED for the last update."""
         return pico_dyn_last_update_kind(self._d)
+
+    @property
+    def last_update_times(self) -> tuple:
+        """(CSR rebuild ms, coreness-step ms) of the last update."""
+        return pico_dyn_last_update_times(self._d)
 
     def coreness(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.n, dtype=torch.int32, device=self.device)

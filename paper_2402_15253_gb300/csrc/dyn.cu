@@ -967,6 +967,8 @@ struct pico_dyn {
     double full_ms = 0, del_ms = 0, ins_ms = 0;
     long long del_k = 0, ins_k = 0;
     double cd_ms = 0;   // one count of cd over all arcs (insertion passes after deletions)
+    // device time of the last update's CSR rebuild and of its coreness step
+    double last_rebuild_ms = -1, last_coreness_ms = -1;
     // scratch of the coreness steps (deletions, insertion passes, a recomputation),
     // sized for the arc capacity and kept for the state's lifetime
     void *ws2 = nullptr;
@@ -1113,12 +1115,19 @@ pico_dyn *pico_dyn_create(const int64_t *row_ptr, const int32_t *col_idx, int64_
                                cudaMemcpyDeviceToDevice, s) == cudaSuccess;
     ok = ok && (m == 0 || cudaMemcpyAsync(d->ci[0], col_idx, (size_t)m * sizeof(int),
                                           cudaMemcpyDeviceToDevice, s) == cudaSuccess);
+    // the first coreness runs PICO_ALGO_AUTO on the state's scratch, as a
+    // recomputation does, twice: the second run's time, the cost model's
+    // reference, holds no allocation and no first launch of the kernel
     EventTimer full;
-    full.start(s);
-    ok = ok && pico_coreness_i64(reinterpret_cast<const int64_t *>(d->rp[0]), d->ci[0], n, m,
-                                 d->core, PICO_ALGO_AUTO, stream) ==
-                   PICO_OK;
-    full.stop(s);
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+        full.start(s);
+        if (m > 0)
+            ok = pico::launch_hybrid<long long>(d->rp[0], d->ci[0], n, m, d->core, d->ws2, last,
+                                                s, cfg) == 0;
+        else
+            ok = cudaMemsetAsync(d->core, 0, (size_t)n * sizeof(int), s) == cudaSuccess;
+        full.stop(s);
+    }
     // cd for the first insertion batch: one count over all arcs
     EventTimer count;
     count.start(s);
@@ -1214,6 +1223,8 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
         return pico::launch_cooperative((const void *)pico::dyn::scan_kernel, dim3(cfg.sms),
                                            dim3(pico::kThreads), args, 0, s) == cudaSuccess;
     };
+    EventTimer trebuild;
+    trebuild.start(s);
     bool ok = cudaMemsetAsync(ws, 0, zero_bytes, s) == cudaSuccess;
     if (ok) {
         pico::dyn::count_kernel<<<G, 256, 0, s>>>(ins, n_ins, del, n_del, n, ins_cnt, del_cnt,
@@ -1235,6 +1246,7 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
         pico::dyn::check_kernel<<<G, 256, 0, s>>>(T, tp + n, nrp, cursor, err);
         ok = cudaGetLastError() == cudaSuccess;
     }
+    trebuild.stop(s);
     int herr = 0;
     ok = ok && sync_status(s) == PICO_OK &&
          cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
@@ -1245,6 +1257,8 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
         return !ok ? PICO_ERR_CUDA : PICO_ERR_BAD_GRAPH;   // the state is unchanged
     }
     // the graph is consistent: switch to it and bring the coreness up to date
+    d->last_rebuild_ms = trebuild.ms();
+    d->last_coreness_ms = -1;
     d->cur = 1 - d->cur;
     d->m = m_new;
     const bool cd_was_valid = d->cd_valid;
@@ -1286,6 +1300,7 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
         if (sync_status(s) != PICO_OK) return PICO_ERR_CUDA;
         const double t = full.ms();
         if (t > 0) d->full_ms = t;
+        d->last_coreness_ms = t;
         d->last_kind = PICO_DYN_RECOMPUTED;
         return pico_last_device_status(stream);   // cd stays invalid: the next insertion
     }                                             // batch recounts it
@@ -1310,6 +1325,7 @@ int pico_dyn_update(pico_dyn *d, const int32_t *ins, int64_t n_ins, const int32_
     }
     if (sync_status(s) != PICO_OK) return PICO_ERR_CUDA;
     const int st = pico_last_device_status(stream);
+    d->last_coreness_ms = tdel.ms() + tins.ms();
     d->cd_valid = st == PICO_OK && n_ins > 0;
     d->last_kind = PICO_DYN_MAINTAINED;
     if (st == PICO_OK) {
@@ -1337,6 +1353,14 @@ int pico_dyn_last_update_kind(pico_dyn *d)
 {
     if (!d) return PICO_ERR_INVALID_ARG;
     return d->last_kind;
+}
+
+int pico_dyn_last_update_times(pico_dyn *d, double *rebuild_ms, double *coreness_ms)
+{
+    if (!d || !rebuild_ms || !coreness_ms) return PICO_ERR_INVALID_ARG;
+    *rebuild_ms = d->last_rebuild_ms;
+    *coreness_ms = d->last_coreness_ms;
+    return PICO_OK;
 }
 
 int pico_dyn_coreness(pico_dyn *d, int32_t *out_core, pico_stream_t stream)

@@ -43,6 +43,8 @@
 // or overshoot-plus-add-back pairs).
 #pragma once
 
+#include <type_traits>
+
 #include "pico_device.cuh"
 
 namespace pico {
@@ -396,6 +398,66 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
         repair(p, prev_k, r_s0, r_e0, r_s1, r_e1, tid, nthreads);
 }
 
+// With int32 offsets a dynamic chunk entry holds its arc range [s, t), so
+// that its walk needs no row bounds (one dependent load less per chunk);
+// with int64 offsets it holds (vertex, chunk index), as the scan's entries
+// do.
+template <typename Off>
+struct RangeEntries : std::integral_constant<bool, sizeof(Off) == 4> {};
+
+// Warp-cooperative append of the arc ranges of large vertices: every lane
+// with `pred` owns a vertex whose row starts at rs and holds d arcs; the warp
+// writes the ceil(d / chunk) ranges of each such vertex in turn.
+__device__ __forceinline__ void warp_push_ranges(bool pred, int rs, int d, int2 *list,
+                                                 unsigned *counter, unsigned cap, Ctrl *ctl,
+                                                 int chunk)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned m = __ballot_sync(kFull, pred);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int s0 = __shfl_sync(kFull, rs, src);
+        const int dd = __shfl_sync(kFull, d, src);
+        const unsigned nch = (unsigned)((dd + chunk - 1) / chunk);
+        unsigned pos = 0;
+        if (lane == 0) pos = atomicAdd(counter, nch);
+        pos = __shfl_sync(kFull, pos, 0);
+        if ((unsigned long long)pos + nch > cap) {
+            if (lane == 0) set_error(ctl, kErrNotConverged);
+            continue;
+        }
+        for (unsigned c = lane; c < nch; c += 32) {
+            const int a = s0 + (int)c * chunk;
+            const int b = dd - (int)c * chunk > chunk ? a + chunk : s0 + dd;
+            st_relaxed(list + pos + c, make_int2(a, b));
+        }
+    }
+}
+
+// One warp walks the arcs [s, t) of col_idx (a range entry).
+template <typename F>
+__device__ __forceinline__ void walk_range(const int *__restrict__ ci, int s, int t, F &f)
+{
+    constexpr int U = F::kArcs;
+    const int lane = threadIdx.x & 31;
+    for (int e0 = s; e0 < t; e0 += 32 * U) {
+        bool valid[U];
+        int vo[U], u[U], ao[U], bo[U], rso[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const int e = e0 + 32 * j + lane;
+            valid[j] = e < t;
+            u[j] = valid[j] ? __ldg(ci + e) : -1;
+            vo[j] = -1;
+            rso[j] = 0;
+            ao[j] = 0;
+            bo[j] = 0;
+        }
+        f.arcs(valid, vo, u, rso, ao, bo);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // PeelOne with asynchronous levels (the whole grid, one graph)
 // ---------------------------------------------------------------------------
@@ -418,7 +480,7 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
 //            appends u: to 32 local slots of its warp (shared memory) while
 //            they last, else to the queue qs. A vertex's degree class is
 //            decided when it is walked: one above small_deg is then listed as
-//            chunk entries in qb. Queue slots start as -1 (set at launch) and
+//            chunk entries in qb (arc ranges with int32 offsets). Queue slots start as -1 (set at launch) and
 //            are written once in the whole run. Every warp holds a ticket of
 //            32 consecutive qs slots and one of one qb slot; each pass of its
 //            loop walks what has arrived in them plus at most one batch of its
@@ -608,7 +670,11 @@ __device__ void run_async(const Params<Off> &p, GridDom &dom, unsigned *s_tmp,
                 d = (long long)(p.rp[v + 1] - rs);
             }
             const bool large = d > p.tn.small_deg;
-            warp_push_chunks<true>(large, v, d, p.qb, &live[L_QB], p.qb_cap, ctl, p.tn.chunk);
+            if (RangeEntries<Off>::value)
+                warp_push_ranges(large, (int)rs, (int)d, p.qb, &live[L_QB], p.qb_cap, ctl,
+                                 p.tn.chunk);
+            else
+                warp_push_chunks<true>(large, v, d, p.qb, &live[L_QB], p.qb_cap, ctl, p.tn.chunk);
             walk_batch(p.ci, large ? -1 : v, rs, large ? 0 : (int)d, f);
         };
 
@@ -656,8 +722,6 @@ __device__ void run_async(const Params<Off> &p, GridDom &dom, unsigned *s_tmp,
                 worked = true;
             }
             probe = __shfl_sync(kFull, probe, 0);
-            e.x = __shfl_sync(kFull, e.x, 0);
-            e.y = __shfl_sync(kFull, e.y, 0);
             if (probe >= 0) {   // read the whole ticket
                 const unsigned sl = ts + lane;
                 int v = -1;
@@ -680,16 +744,21 @@ __device__ void run_async(const Params<Off> &p, GridDom &dom, unsigned *s_tmp,
                     }
                 }
             }
+            e.x = __shfl_sync(kFull, e.x, 0);
+            e.y = __shfl_sync(kFull, e.y, 0);
             if (e.x >= 0 && e.y >= 0) {   // both words of the chunk entry written
                 if (!busy) {
                     if (lane == 0) atomicAdd(&s_busy, 1u);
                     busy = true;
                 }
-                walk_chunk(p.rp, p.ci, e.x, e.y, f, p.tn);
+                unsigned nt = 0;   // the next ticket, taken while this entry is walked
+                if (lane == 0) nt = atomicAdd(qb_head, 1u);
+                if constexpr (RangeEntries<Off>::value)
+                    walk_range(p.ci, e.x, e.y, f);
+                else
+                    walk_chunk(p.rp, p.ci, e.x, e.y, f, p.tn);
                 walked += 1;
                 worked = true;
-                unsigned nt = 0;
-                if (lane == 0) nt = atomicAdd(qb_head, 1u);
                 tb = __shfl_sync(kFull, nt, 0);
             }
             if (worked || f.loc_n) {

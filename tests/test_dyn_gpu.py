@@ -234,6 +234,7 @@ def test_recomputation_fallback(pico, policy):
     dg = pico.DynamicGraph(g.row_ptr.cuda(), g.col_idx.cuda(), capacity_arcs=2 * len(edges) + 20000)
     pol = {"recompute": pico.PICO_DYN_RECOMPUTE, "auto": pico.PICO_DYN_AUTO}[policy]
     kinds = []
+    assert dg.last_update_times == (-1.0, -1.0)
     for step, (ki, kd) in enumerate([(300, 0), (0, 300), (400, 400), (200, 0), (2000, 2000)]):
         dg.set_policy(pol if step != 3 else pico.PICO_DYN_MAINTAIN)
         ins, dele = random_batch(rng, n, edges, ki, kd)
@@ -241,6 +242,8 @@ def test_recomputation_fallback(pico, policy):
         edges = (edges - set(dele)) | set(ins)
         check(pico, dg, n, edges)
         kinds.append(dg.last_update_kind)
+        rebuild_ms, step_ms = dg.last_update_times   # both phases were timed
+        assert rebuild_ms > 0 and step_ms > 0
     assert kinds[3] == pico.PICO_DYN_MAINTAINED   # insertion passes right after a recompute
     if policy == "recompute":
         assert kinds[:3] == [pico.PICO_DYN_RECOMPUTED] * 3 and kinds[4] == pico.PICO_DYN_RECOMPUTED
