@@ -61,6 +61,10 @@ int device_state(DeviceState **out)
         d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk, pico::kClusterLog2};
         d.cfg.batched_threads = pico::kThreads;
         d.cfg.peel_async = env_ll("PICO_PEEL_WAVES", 0) == 0;
+        // PICO_PEEL_GUARD=G: PeelOne reads a neighbour before decrementing it
+        // in the chunks of vertices of degree > G * k (0: never)
+        if (const char *g = std::getenv("PICO_PEEL_GUARD"); g && *g)
+            d.cfg.tn.peel_guard = std::max(0, std::atoi(g));
         // With PICO_L2_PERSIST=1, the L2 set-aside for persisting lines (a
         // limit of this process's context) is raised to the device maximum,
         // and the PeelOne launches mark their residual degrees persisting and

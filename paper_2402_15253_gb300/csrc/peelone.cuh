@@ -131,6 +131,8 @@ struct Arc {
     int *out = nullptr;   // run_async: receives k for every vertex queued at level k
     int *loc = nullptr;   // run_async: this warp's 32 shared-memory slots for the small
     unsigned loc_n = 0;   // vertices it walks itself next (warp-uniform count)
+    bool hub = false;     // run_async: this walk reads each neighbour before its
+                          // decrement (warp-uniform; chunks of high-degree vertices)
     unsigned long long n_arcs = 0, n_atomics = 0, n_extra = 0;
 
     __device__ __forceinline__ bool item(int, int &, int &) { return true; }
@@ -144,9 +146,14 @@ struct Arc {
         // work array's values matter only while a vertex is unqueued, and a
         // decrement of a queued vertex returns at most k (no append). One
         // dependent round trip less per arc.
+        // A hub's chunk still reads first: most of its arcs end at vertices
+        // peeled earlier, and a load costs L2 less than an atomic.
         constexpr bool kGuard = !(kAsync && Mode == kPeelRepair);
+        const bool guard = kGuard || hub;
 #pragma unroll
-        for (int j = 0; j < kArcs; ++j) c[j] = valid[j] ? (kGuard ? __ldca(core + u[j]) : INT_MAX) : 0;
+        for (int j = 0; j < kArcs; ++j)
+            c[j] = valid[j] ? (guard ? (kGuard ? __ldca(core + u[j]) : __ldcg(core + u[j])) : INT_MAX)
+                            : 0;
 #pragma unroll
         for (int j = 0; j < kArcs; ++j) {
             old[j] = 0;
@@ -405,10 +412,19 @@ __device__ void run(const Params<Off> &p, Dom &dom, unsigned *s_tmp, unsigned lo
 template <typename Off>
 struct RangeEntries : std::integral_constant<bool, sizeof(Off) == 4> {};
 
+// Whether the chunks of a vertex of degree d peeled at level k read each
+// neighbour before decrementing it (see kPeelGuard).
+__device__ __forceinline__ bool hub_guard(long long d, int k, int g)
+{
+    return g > 0 && d > (long long)g * k;
+}
+
 // Warp-cooperative append of the arc ranges of large vertices: every lane
 // with `pred` owns a vertex whose row starts at rs and holds d arcs; the warp
-// writes the ceil(d / chunk) ranges of each such vertex in turn.
-__device__ __forceinline__ void warp_push_ranges(bool pred, int rs, int d, int2 *list,
+// writes the ceil(d / chunk) ranges [a, b) of each such vertex in turn, as
+// (a, b), or as (a, ~b) when `guard` is set (b >= 1, so ~b <= -2 never
+// equals the empty slot's -1).
+__device__ __forceinline__ void warp_push_ranges(bool pred, int rs, int d, bool guard, int2 *list,
                                                  unsigned *counter, unsigned cap, Ctrl *ctl,
                                                  int chunk)
 {
@@ -419,6 +435,7 @@ __device__ __forceinline__ void warp_push_ranges(bool pred, int rs, int d, int2 
         m &= m - 1;
         const int s0 = __shfl_sync(kFull, rs, src);
         const int dd = __shfl_sync(kFull, d, src);
+        const bool gg = __shfl_sync(kFull, (int)guard, src) != 0;
         const unsigned nch = (unsigned)((dd + chunk - 1) / chunk);
         unsigned pos = 0;
         if (lane == 0) pos = atomicAdd(counter, nch);
@@ -430,7 +447,7 @@ __device__ __forceinline__ void warp_push_ranges(bool pred, int rs, int d, int2 
         for (unsigned c = lane; c < nch; c += 32) {
             const int a = s0 + (int)c * chunk;
             const int b = dd - (int)c * chunk > chunk ? a + chunk : s0 + dd;
-            st_relaxed(list + pos + c, make_int2(a, b));
+            st_relaxed(list + pos + c, make_int2(a, gg ? ~b : b));
         }
     }
 }
@@ -458,6 +475,38 @@ __device__ __forceinline__ void walk_range(const int *__restrict__ ci, int s, in
     }
 }
 
+// One warp walks chunk c of the adjacency of vertex v (a (vertex, chunk)
+// entry), reading each neighbour first when v's degree calls for it.
+template <typename Off, typename F>
+__device__ __forceinline__ void walk_chunk_guarded(const Off *__restrict__ rp,
+                                                   const int *__restrict__ ci, int v, int c, F &f,
+                                                   const Tuning &tn)
+{
+    constexpr int U = F::kArcs;
+    const int lane = threadIdx.x & 31;
+    const Off rs = rp[v], re = rp[v + 1];
+    const Off s = rs + (Off)c * tn.chunk;
+    const Off t = (s + tn.chunk < re) ? s + tn.chunk : re;
+    f.hub = hub_guard((long long)(re - rs), f.k, tn.peel_guard);
+    for (Off e0 = s; e0 < t; e0 += 32 * U) {
+        bool valid[U];
+        int vo[U], u[U], ao[U], bo[U];
+        Off rso[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const Off e = e0 + 32 * j + lane;
+            valid[j] = e < t;
+            u[j] = valid[j] ? __ldg(ci + e) : -1;
+            vo[j] = v;
+            rso[j] = rs;
+            ao[j] = 0;
+            bo[j] = 0;
+        }
+        f.arcs(valid, vo, u, rso, ao, bo);
+    }
+    f.hub = false;
+}
+
 // ---------------------------------------------------------------------------
 // PeelOne with asynchronous levels (the whole grid, one graph)
 // ---------------------------------------------------------------------------
@@ -475,7 +524,13 @@ __device__ __forceinline__ void walk_range(const int *__restrict__ ci, int s, in
 //            before a decrement: the decrement's return value decides.
 //   barrier  its last arrival sets the ticket heads (below) and snapshots
 //            the counters; the scan's frontier is then final.
-//   static   the scan's frontier is walked like one wave (expand).
+//   static   the scan's frontier is walked like one wave (as expand() does).
+//   hubs     a chunk of a vertex whose degree exceeds tn.peel_guard * k reads
+//            each neighbour's residual degree before the decrement and skips
+//            the atomic when it is <= k: such a vertex has about k neighbours
+//            left, so most of its arcs end at vertices peeled earlier, and a
+//            load costs L2 less than an atomic. Other walks issue the
+//            decrement at once (no dependent round trip on a chain).
 //   dynamic  the decrement that takes u from k + 1 to k writes out[u] = k and
 //            appends u: to 32 local slots of its warp (shared memory) while
 //            they last, else to the queue qs. A vertex's degree class is
@@ -671,21 +726,32 @@ __device__ void run_async(const Params<Off> &p, GridDom &dom, unsigned *s_tmp,
             }
             const bool large = d > p.tn.small_deg;
             if (RangeEntries<Off>::value)
-                warp_push_ranges(large, (int)rs, (int)d, p.qb, &live[L_QB], p.qb_cap, ctl,
-                                 p.tn.chunk);
+                warp_push_ranges(large, (int)rs, (int)d, hub_guard(d, k, p.tn.peel_guard), p.qb,
+                                 &live[L_QB], p.qb_cap, ctl, p.tn.chunk);
             else
                 warp_push_chunks<true>(large, v, d, p.qb, &live[L_QB], p.qb_cap, ctl, p.tn.chunk);
             walk_batch(p.ci, large ? -1 : v, rs, large ? 0 : (int)d, f);
         };
 
-        // static part: the scan's frontier, walked like one wave
+        // static part: the scan's frontier, walked like one wave (batches of
+        // small vertices, then (vertex, chunk) entries)
         const unsigned vb = batch_width(nfs, nfb, nwarps);
-        expand(p.rp, p.ci, p.fs, nfs, p.fb, nfb, gwarp, nwarps, f, p.tn, vb);
         unsigned long long walked = 0;   // listed entries walked, not yet added to `done`
         {
             const unsigned nbatch = (nfs + vb - 1u) / vb;
-            for (unsigned unit = gwarp; unit < nbatch + nfb; unit += nwarps)
-                walked += unit < nbatch ? min(vb, nfs - unit * vb) : 1u;
+            for (unsigned unit = gwarp; unit < nbatch + nfb; unit += nwarps) {
+                if (unit < nbatch) {
+                    const unsigned idx = unit * vb + lane;
+                    int v = -1;
+                    if (lane < vb && idx < nfs) v = ldcg(p.fs + idx);
+                    walk_small_batch(p.rp, p.ci, v, f, p.tn.small_deg);
+                    walked += min(vb, nfs - unit * vb);
+                } else {
+                    const int2 ent = __ldcg(p.fb + (unit - nbatch));   // written by other CTAs
+                    walk_chunk_guarded(p.rp, p.ci, ent.x, ent.y, f, p.tn);
+                    walked += 1;
+                }
+            }
         }
 
         // dynamic part. Each pass walks what has arrived in this warp's
@@ -746,17 +812,20 @@ __device__ void run_async(const Params<Off> &p, GridDom &dom, unsigned *s_tmp,
             }
             e.x = __shfl_sync(kFull, e.x, 0);
             e.y = __shfl_sync(kFull, e.y, 0);
-            if (e.x >= 0 && e.y >= 0) {   // both words of the chunk entry written
+            if (e.x >= 0 && e.y != -1) {   // both words of the chunk entry written
                 if (!busy) {
                     if (lane == 0) atomicAdd(&s_busy, 1u);
                     busy = true;
                 }
                 unsigned nt = 0;   // the next ticket, taken while this entry is walked
                 if (lane == 0) nt = atomicAdd(qb_head, 1u);
-                if constexpr (RangeEntries<Off>::value)
-                    walk_range(p.ci, e.x, e.y, f);
-                else
-                    walk_chunk(p.rp, p.ci, e.x, e.y, f, p.tn);
+                if constexpr (RangeEntries<Off>::value) {
+                    f.hub = e.y < 0;
+                    walk_range(p.ci, e.x, e.y < 0 ? ~e.y : e.y, f);
+                    f.hub = false;
+                } else {
+                    walk_chunk_guarded(p.rp, p.ci, e.x, e.y, f, p.tn);
+                }
                 walked += 1;
                 worked = true;
                 tb = __shfl_sync(kFull, nt, 0);

@@ -45,12 +45,21 @@ constexpr long long kPullMinArcs = 1ll << 22;  // ... of a graph with at least t
 // add-back.
 enum : int { kPeelRepair = 0, kPeelCas = 1, kPeelAddBack = 2 };
 
+// PeelOne's asynchronous levels issue a decrement for every arc without
+// reading the neighbour first. A vertex peeled at level k has about k
+// neighbours left, so when its degree is well above k most of its arcs end at
+// vertices peeled earlier. Chunks of a vertex with degree > kPeelGuard * k
+// read the neighbour's residual degree first and skip the atomic when it is
+// <= k (0: never).
+constexpr int kPeelGuard = 4;
+
 struct Tuning {
     int small_deg;
     int chunk;
     int cluster_log2;   // batched form: graphs with >= 2^cluster_log2 arcs use a cluster
     int update_mode = kUpdateAuto;
     int pull_pct = kPullPct;
+    int peel_guard = kPeelGuard;   // PeelOne: guard the arcs of vertices of degree > peel_guard * k
 };
 constexpr int kClusterNever = 62;   // cluster_log2 value that disables clusters
 constexpr int kClusterLog2 = 21;    // default
