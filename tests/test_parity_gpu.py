@@ -173,6 +173,57 @@ def test_families_match_oracle(pico, algo, name, make):
         assert st["atomics"] == g.arcs + 2 * ost["updates"]
 
 
+# --------------------------------------------------------------------------
+# PeelOne's level structure: many consecutive levels, gaps between levels
+# (empty levels skipped), a hub whose residual degree falls through many
+# values before its level, thousands of vertices reaching one value, and a
+# dense R-MAT core; int32 and int64 offsets (arc-range and (vertex, chunk)
+# entries for large vertices)
+# --------------------------------------------------------------------------
+
+def _cliques(sizes):
+    """Disjoint union of complete graphs K_s (coreness s - 1 each)."""
+    return gg.disjoint_union([gg.complete_graph(s) for s in sizes])
+
+
+def _hub_over_cliques(n_cliques, s, leaves):
+    """K_s copies whose vertex 0 all join one hub, which also has `leaves`
+    leaves: the hub's residual degree falls through many values."""
+    edges, base = [], 0
+    for _ in range(n_cliques):
+        edges += [(base + i, base + j) for i in range(s) for j in range(i + 1, s)]
+        base += s
+    hub = base
+    edges += [(hub, c * s) for c in range(n_cliques)]
+    edges += [(hub, hub + 1 + i) for i in range(leaves)]
+    return gg.from_edge_list(edges, hub + 1 + leaves)
+
+
+LEVEL_CASES = [
+    ("consecutive-1..40", lambda: _cliques(list(range(2, 42)) * 3)),
+    ("gaps", lambda: _cliques([2, 4, 8, 20, 21, 56, 57, 91, 130] * 4)),
+    ("hub-over-cliques", lambda: _hub_over_cliques(60, 12, 30)),
+    ("many-at-one-value", lambda: gg.disjoint_union([gg.path_graph(10)] +
+                                                  [gg.complete_graph(5)] * 5000)),
+    ("rmat12-ef32", lambda: gg.rmat_graph(12, 32, 41)),
+]
+
+
+@pytest.mark.parametrize("off", [None, torch.int64], ids=["int32", "int64"])
+@pytest.mark.parametrize("name,make", LEVEL_CASES, ids=[c[0] for c in LEVEL_CASES])
+def test_peelone_level_structure(pico, name, make, off):
+    g = make()
+    rp, ci = g.numpy()
+    want = oracle.bz_coreness(rp, ci)
+    got, st = run(pico, g, "peelone", off)
+    assert_same(got, want, f"{name} peelone")
+    _, ost = oracle.peelone(rp, ci)
+    assert st["levels"] == ost["levels"]
+    assert st["kmax"] == ost["kmax"]
+    assert st["arcs"] == ost["arcs_scanned"]
+    assert st["atomics"] - st["extra"] == ost["decrements"]
+
+
 @pytest.fixture
 def update_mode(pico):
     """Sets the UpdateHisto direction for one test, then restores auto."""
