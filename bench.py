@@ -308,14 +308,18 @@ def autotune_default():
     return autotune.DEFAULT
 
 
-def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int = 256,
-                budget_gb: float = 40.0):
+def bench_serve(pico, dev, requests: int, plain_requests: int = 2000, loads=(0.5, 0.8, 0.95),
+                pool_size: int = 256, budget_gb: float = 40.0):
     """Served form: a Poisson stream of requests drawn from the batch size
     distribution (log-uniform 100..200,000 vertices, half ER, half R-MAT)
     plus 5% R-MAT scale 20 outliers, replayed open-loop into the request
     server (continuous batching, 40 GB admission budget) at 0.5/0.8/0.95 of
     its measured capacity, next to the sequential plain path (one
-    single-graph call per request, one at a time) at the same loads.
+    single-graph call per request, one at a time) at the same offered rates.
+    The server takes `requests` requests per run; the plain path, which is
+    overloaded at every one of these rates (its latency grows with the
+    stream's length), takes the first `plain_requests` of the same stream.
+    All server runs come first, then the plain runs.
     Latency = completion - arrival, host clock, including the host-to-device
     copy of each CSR and the copy of its result back."""
     import math
@@ -335,54 +339,59 @@ def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int
         out = torch.zeros(max(g.n, 1), dtype=torch.int32).pin_memory()
         pool.append((g.n, g.arcs, rp, ci, out))
     regular, outliers = list(range(pool_size - n_out)), list(range(pool_size - n_out, pool_size))
+    total = max(requests, plain_requests)
     pick = []
-    for i in range(requests):
+    for i in range(total):
         u = gg.unit_int(gg.SEED_BASE + 5, gg.S_SERVE, 2 * i)
         v = gg.unit_int(gg.SEED_BASE + 5, gg.S_SERVE, 2 * i + 1)
         lst = outliers if u < 0.05 else regular
         pick.append(lst[min(len(lst) - 1, int(v * len(lst)))])
     expo = [-math.log(1.0 - gg.unit_int(gg.SEED_BASE + 5, gg.S_SERVE + 1, i))
-            for i in range(requests)]
+            for i in range(total)]
     budget = int(budget_gb * (1 << 30))
 
     def run(rate, single):
+        count = plain_requests if single else requests
         cfg = (1, 1, 1) if single else (4, 512, 0)
         srv = pico.pico_server_create(budget, 0, cfg[0], cfg[1], cfg[2])
         if not srv:
             raise RuntimeError("pico_server_create failed")
         t0 = pico.pico_clock_ns() + 2_000_000
         arr, t = [], 0.0
-        for i in range(requests):
+        for i in range(count):
             if rate is not None:
                 t += expo[i] / rate
             arr.append(t0 + int(t * 1e9))
-        for i, j in enumerate(pick):
+        for i, j in enumerate(pick[:count]):
             n, m, rp, ci, out = pool[j]
             if pico.pico_server_submit(srv, rp, ci, n, m, out, arr[i]) < 0:
                 raise RuntimeError("submit failed")
         rc = pico.pico_server_drain(srv)
-        tk = torch.zeros(requests, dtype=torch.int64)
-        dn = torch.zeros(requests, dtype=torch.int64)
-        k = pico.pico_server_poll(srv, tk, dn, requests)
+        tk = torch.zeros(count, dtype=torch.int64)
+        dn = torch.zeros(count, dtype=torch.int64)
+        k = pico.pico_server_poll(srv, tk, dn, count)
         pico.pico_server_destroy(srv)
-        if rc != 0 or k != requests:
+        if rc != 0 or k != count:
             raise RuntimeError(f"server failed rc={rc} done={k}")
         arr_t = torch.tensor(arr, dtype=torch.int64)[tk]
         lat = (dn - arr_t).double() / 1e6
         span = (int(dn.max()) - int(torch.tensor(arr).min())) / 1e9
-        return {"graphs_per_s": requests / span, "p50_ms": float(lat.quantile(0.5)),
-                "p99_ms": float(lat.quantile(0.99)), "mean_ms": float(lat.mean())}
+        return {"requests": count, "graphs_per_s": count / span,
+                "p50_ms": float(lat.quantile(0.5)), "p99_ms": float(lat.quantile(0.99)),
+                "mean_ms": float(lat.mean())}
 
     pico.pico_set_tuning(*autotune_default())
     capacity = run(None, False)["graphs_per_s"]
-    res = {"workload": f"{requests} requests, Poisson arrivals, pool of {pool_size} graphs "
+    res = {"workload": f"{requests} requests (plain path: the first {plain_requests}), Poisson "
+                       f"arrivals, pool of {pool_size} graphs "
                        f"(log-uniform 100..200,000 vertices, half ER, half R-MAT; "
                        f"{n_out} R-MAT scale 20 drawn with probability 0.05)",
            "budget_gb": budget_gb, "capacity_graphs_per_s": capacity, "loads": {}}
     for f in loads:
-        rate = f * capacity
-        res["loads"][str(f)] = {"offered_graphs_per_s": rate, "served": run(rate, False),
-                                "sequential_plain": run(rate, True)}
+        res["loads"][str(f)] = {"offered_graphs_per_s": f * capacity,
+                                "served": run(f * capacity, False)}
+    for f in loads:
+        res["loads"][str(f)]["sequential_plain"] = run(f * capacity, True)
     # the result buffer of every requested pool graph (written by the last
     # request for that graph) must hold the oracle's coreness; checked after
     # the timed runs
@@ -394,7 +403,7 @@ def bench_serve(pico, dev, requests: int, loads=(0.5, 0.8, 0.95), pool_size: int
         want = oracle.bz_coreness(rp.numpy().astype("int64"), ci.numpy()[:m])
         return bool((out[:n].numpy() == want).all())
 
-    asked = sorted(set(pick))
+    asked = sorted(set(pick[:total]))
     with ThreadPoolExecutor(max_workers=16) as ex:
         ok = list(ex.map(check, asked))
     if not all(ok):
@@ -772,8 +781,10 @@ def main():
                     help="'auto' (autotune each method on the graph) or S,C,T,K: small_deg, "
                          "chunk, batched CTA threads, cluster log2 arcs, for both methods "
                          "(or PeelOne's/HistoCore's, separated by '/')")
-    ap.add_argument("--serve-requests", type=int, default=2000,
-                    help="requests of the served-form measurement (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=6000,
+                    help="requests of each served-form run (0: skip the served form)")
+    ap.add_argument("--plain-requests", type=int, default=2000,
+                    help="requests of each run of the sequential plain path beside it")
     ap.add_argument("--no-partitioned", action="store_true",
                     help="skip partitioned HistoCore on the workload graph")
     ap.add_argument("--no-configs", action="store_true",
@@ -1010,7 +1021,7 @@ def main():
     if rank == 0 and not args.no_partitioned:
         line["partitioned"] = bench_partitioned(pico, g, out["histocore"])
     if rank == 0 and args.serve_requests > 0:
-        line["served"] = bench_serve(pico, dev, args.serve_requests)
+        line["served"] = bench_serve(pico, dev, args.serve_requests, args.plain_requests)
     h_csr = None   # host copy of the workload graph for the CPU baseline
     if (rank == 0 and ws == 1 and not args.no_cpu_baseline
             and CPU_SAMPLE.get(args.workload) == args.workload):
