@@ -381,6 +381,7 @@ def bench_serve(pico, dev, requests: int, plain_requests: int = 2000, loads=(0.5
                 "mean_ms": float(lat.mean())}
 
     pico.pico_set_tuning(*autotune_default())
+    run(None, False)   # warm-up: first launches, the memory pool's growth
     capacity = run(None, False)["graphs_per_s"]
     res = {"workload": f"{requests} requests (plain path: the first {plain_requests}), Poisson "
                        f"arrivals, pool of {pool_size} graphs "
@@ -643,6 +644,8 @@ def bench_maintenance(pico, g, stream, k: int = 10000, seed: int = 0x9C6,
         if len(dele) == 2 * k:
             break
     dev = g.row_ptr.device
+    if update_tuning:   # the state times its first full computation at creation
+        pico.pico_set_tuning(*update_tuning)
     dg = pico.DynamicGraph(g.row_ptr, g.col_idx, capacity_arcs=g.arcs + 4 * k + 1024)
     batches = {"insert": (ins[:k], []), "delete": ([], dele[:k]),
                "mixed": (ins[k:2 * k], dele[k:2 * k])}
@@ -1011,11 +1014,11 @@ def main():
                                             {a: statistics.median(v) for a, v in per.items()},
                                             stream)
     if rank == 0 and not args.no_maintenance:
-        # the updates run every kind of kernel (HistoCore for deletions, the
-        # insertion passes, or a recomputation): the default tuning
-        line["maintenance"] = bench_maintenance(
-            pico, g, stream, update_tuning=autotune_default(),
-            recompute_tuning=tuned[line["auto"]["method"]] if rank == 0 else None)
+        # the updates and the recomputations they are compared with run with
+        # the same tuning: the one tuned for the method AUTO picks here
+        t_auto = tuned[line["auto"]["method"]]
+        line["maintenance"] = bench_maintenance(pico, g, stream, update_tuning=t_auto,
+                                                recompute_tuning=t_auto)
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(pico, dev, stream, args.batch_graphs)
     if rank == 0 and not args.no_partitioned:

@@ -346,7 +346,10 @@ void pico_dyn_destroy(pico_dyn *d);
  * those batches were within a factor of two of this one in size (otherwise
  * the batch is maintained, and measured); insertion passes that follow
  * deletions add one count of neighbour estimates over all arcs, timed when
- * the state was created. PICO_DYN_MAINTAIN always
+ * the state was created. A batch with both deletions and insertions is
+ * predicted from the last such batch of a similar size, or else from the two
+ * steps' separate times with a 25 % surcharge (its insertion passes search
+ * wider regions after the deletions). PICO_DYN_MAINTAIN always
  * maintains, PICO_DYN_RECOMPUTE always recomputes. The result is the same
  * coreness either way. pico_dyn_last_update_kind reports what the last update
  * did (PICO_DYN_MAINTAINED or PICO_DYN_RECOMPUTED; after a recomputation
