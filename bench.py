@@ -388,6 +388,11 @@ def bench_serve(pico, dev, requests: int, plain_requests: int = 2000, loads=(0.5
                        f"(log-uniform 100..200,000 vertices, half ER, half R-MAT; "
                        f"{n_out} R-MAT scale 20 drawn with probability 0.05)",
            "budget_gb": budget_gb, "capacity_graphs_per_s": capacity, "loads": {}}
+    # every request copies its CSR to the device and its result back: at
+    # capacity these copies alone need this much of the host link
+    io = [4 * (pool[j][0] + 1) + 4 * pool[j][1] + 4 * pool[j][0] for j in pick[:requests]]
+    res["copy_bytes_per_request"] = sum(io) / len(io)
+    res["copy_gbs_at_capacity"] = capacity * res["copy_bytes_per_request"] / 1e9
     for f in loads:
         res["loads"][str(f)] = {"offered_graphs_per_s": f * capacity,
                                 "served": run(f * capacity, False)}
