@@ -104,6 +104,40 @@ int pico_coreness_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n,
                       int32_t *out_core, int algo, pico_stream_t stream);
 
 /*
+ * Input validation (no counterpart in the paper, which takes simple
+ * undirected graphs as given, Sec. II-A). Checks on the device that
+ * (row_ptr, col_idx) is a graph the compute entry points are specified for,
+ * and reports what it found as PICO_DEFECT_* bits:
+ *   ROWS       row_ptr[0] != 0, row_ptr decreasing somewhere, or
+ *              row_ptr[n] != m (the arcs are then not examined);
+ *   IDS        a neighbour id outside [0, n);
+ *   LOOP       a self-loop (v, v);
+ *   ORDER      a row not strictly increasing: unsorted, or a duplicate arc;
+ *   ASYMMETRIC an arc (v, u) without its reverse (u, v).
+ * Validation requires sorted rows; the compute entry points themselves do
+ * not (an unsorted but otherwise valid graph is reported as ORDER).
+ * Every access is bounds-checked, so any input of the stated sizes is safe
+ * to validate. defects: optional host pointer receiving the OR of the bits
+ * (0 for a valid graph). The call synchronises `stream`. Returns PICO_OK,
+ * PICO_ERR_BAD_GRAPH when a defect was found, PICO_ERR_INVALID_ARG for
+ * negative sizes or null pointers, PICO_ERR_OOM or PICO_ERR_CUDA. n == 0 is
+ * valid iff m == 0 and reads nothing.
+ * With PICO_VALIDATE=1 in the environment (read when a device is first
+ * used), pico_coreness and pico_coreness_i64 validate their graph first and
+ * return PICO_ERR_BAD_GRAPH without computing when a defect is found; they
+ * then synchronise their stream and cannot be captured in a CUDA graph.
+ */
+#define PICO_DEFECT_ROWS 1u
+#define PICO_DEFECT_IDS 2u
+#define PICO_DEFECT_LOOP 4u
+#define PICO_DEFECT_ORDER 8u
+#define PICO_DEFECT_ASYMMETRIC 16u
+int pico_validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                        uint32_t *defects, pico_stream_t stream);
+int pico_validate_graph_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                            uint32_t *defects, pico_stream_t stream);
+
+/*
  * Coreness of G independent graphs packed back to back, in one launch.
  * Coreness is defined per graph (Sec. I), so the result equals G separate
  * calls; each graph must satisfy the single-graph contract and may be empty.

@@ -109,6 +109,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
               L.pico_get_stats, L.pico_version):
         f.restype = i32
     L.pico_version.argtypes = []
+    L.pico_validate_graph.argtypes = [vp, vp, i64, i64, ctypes.POINTER(ctypes.c_uint32), vp]
+    L.pico_validate_graph.restype = i32
+    L.pico_validate_graph_i64.argtypes = [vp, vp, i64, i64, ctypes.POINTER(ctypes.c_uint32), vp]
+    L.pico_validate_graph_i64.restype = i32
     L.pico_coreness_batched.argtypes = [vp, vp, i32, vp, vp, i64, i64, vp, i32, vp]
     L.pico_coreness_batched.restype = i32
     L.pico_workspace_bytes_batched.argtypes = [i32, i64, i64, i32]
@@ -207,6 +211,27 @@ def pico_coreness(row_ptr, col_idx, n: int, m: int, out_core, algo: int, stream=
 def pico_coreness_i64(row_ptr, col_idx, n: int, m: int, out_core, algo: int, stream=None) -> int:
     return load().pico_coreness_i64(_ptr(row_ptr), _ptr(col_idx), n, m, _ptr(out_core), algo,
                                     _stream(stream))
+
+
+# defect bits of pico_validate_graph
+PICO_DEFECT_ROWS, PICO_DEFECT_IDS, PICO_DEFECT_LOOP = 1, 2, 4
+PICO_DEFECT_ORDER, PICO_DEFECT_ASYMMETRIC = 8, 16
+
+
+def pico_validate_graph(row_ptr, col_idx, n: int, m: int, stream=None) -> tuple:
+    """Returns (status, PICO_DEFECT_* bits)."""
+    d = ctypes.c_uint32(0)
+    rc = load().pico_validate_graph(_ptr(row_ptr), _ptr(col_idx), n, m, ctypes.byref(d),
+                                    _stream(stream))
+    return rc, d.value
+
+
+def pico_validate_graph_i64(row_ptr, col_idx, n: int, m: int, stream=None) -> tuple:
+    """Returns (status, PICO_DEFECT_* bits)."""
+    d = ctypes.c_uint32(0)
+    rc = load().pico_validate_graph_i64(_ptr(row_ptr), _ptr(col_idx), n, m, ctypes.byref(d),
+                                        _stream(stream))
+    return rc, d.value
 
 
 def pico_coreness_batched(vtx_off, arc_off, G: int, row_ptr, col_idx, total_vertices: int,

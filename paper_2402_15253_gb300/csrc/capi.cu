@@ -61,6 +61,7 @@ int device_state(DeviceState **out)
         d.cfg.tn = pico::Tuning{pico::kSmallDeg, pico::kChunk, pico::kClusterLog2};
         d.cfg.batched_threads = pico::kThreads;
         d.cfg.peel_async = env_ll("PICO_PEEL_WAVES", 0) == 0;
+        d.cfg.validate = env_ll("PICO_VALIDATE", 0) == 1;
         // PICO_PEEL_GUARD=G: PeelOne reads a neighbour before decrementing it
         // in the chunks of vertices of degree > G * k (0: never)
         if (const char *g = std::getenv("PICO_PEEL_GUARD"); g && *g)
@@ -169,6 +170,44 @@ int launch_single(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_
     }
 }
 
+// Validates one graph (see pico_validate_graph): two kernels, then the
+// defect word is read back (the stream is synchronised).
+template <typename Off>
+int validate_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, uint32_t *defects,
+                  cudaStream_t stream)
+{
+    if (defects) *defects = 0;
+    if (n < 0 || m < 0) return PICO_ERR_INVALID_ARG;
+    if (n == 0) {
+        if (m == 0) return PICO_OK;
+        if (defects) *defects = PICO_DEFECT_ROWS;
+        return PICO_ERR_BAD_GRAPH;
+    }
+    if (!rp || (m > 0 && !ci)) return PICO_ERR_INVALID_ARG;
+    if (n >= INT32_MAX || (sizeof(Off) == 4 && m >= INT32_MAX)) return PICO_ERR_INVALID_ARG;
+    DeviceState *d = nullptr;
+    int rc = device_state(&d);
+    if (rc != PICO_OK) return rc;
+    unsigned *flag = nullptr;
+    if (fault_alloc() || cudaMallocAsync(&flag, sizeof(unsigned), stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PICO_ERR_OOM;
+    }
+    unsigned found = 0;
+    bool ok = cudaMemsetAsync(flag, 0, sizeof(unsigned), stream) == cudaSuccess &&
+              pico::launch_validate<Off>(rp, ci, n, m, flag, stream, cfg_of(d)) == 0 &&
+              cudaMemcpyAsync(&found, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, stream) ==
+                  cudaSuccess;
+    cudaFreeAsync(flag, stream);
+    ok = cudaStreamSynchronize(stream) == cudaSuccess && ok;
+    if (!ok) {
+        cudaGetLastError();
+        return PICO_ERR_CUDA;
+    }
+    if (defects) *defects = found;
+    return found ? PICO_ERR_BAD_GRAPH : PICO_OK;
+}
+
 template <typename Off>
 int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_t *out,
                   int algo, cudaStream_t stream)
@@ -182,6 +221,10 @@ int coreness_impl(const Off *rp, const int32_t *ci, int64_t n, int64_t m, int32_
     DeviceState *d = nullptr;
     int rc = device_state(&d);
     if (rc != PICO_OK) return rc;
+    if (cfg_of(d).validate) {   // PICO_VALIDATE=1
+        rc = validate_impl<Off>(rp, ci, n, m, nullptr, stream);
+        if (rc != PICO_OK) return rc;
+    }
     if (m == 0) {   // no arcs: every vertex is isolated
         if (cudaMemsetAsync(out, 0, (size_t)n * sizeof(int32_t), stream) != cudaSuccess) {
             cudaGetLastError();
@@ -231,6 +274,19 @@ int pico_coreness_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n,
 {
     return coreness_impl<long long>(reinterpret_cast<const long long *>(row_ptr), col_idx, n, m,
                                     out_core, algo, (cudaStream_t)stream);
+}
+
+int pico_validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                        uint32_t *defects, pico_stream_t stream)
+{
+    return validate_impl<int>(row_ptr, col_idx, n, m, defects, (cudaStream_t)stream);
+}
+
+int pico_validate_graph_i64(const int64_t *row_ptr, const int32_t *col_idx, int64_t n, int64_t m,
+                            uint32_t *defects, pico_stream_t stream)
+{
+    return validate_impl<long long>(reinterpret_cast<const long long *>(row_ptr), col_idx, n, m,
+                                    defects, (cudaStream_t)stream);
 }
 
 int pico_coreness_batched(const int64_t *vtx_off, const int64_t *arc_off, int32_t G,

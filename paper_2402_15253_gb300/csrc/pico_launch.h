@@ -22,6 +22,7 @@ struct LaunchCfg {
     int batched_threads;           // threads per CTA of the batched kernel (256 or 512)
     bool peel_async = false;       // single-graph PeelOne: asynchronous levels (run_async)
     size_t l2_window = 0;          // largest L2 access-policy window to mark persisting (0: none)
+    bool validate = false;         // single-graph calls validate their graph first (PICO_VALIDATE=1)
 };
 
 // Launches a persistent kernel whose CTAs must all be resident at once (its
@@ -129,6 +130,12 @@ int launch_batched(const int64_t *vtx_off, const int64_t *arc_off, int G, const 
                    int algo, void *ws, LastResult *last, cudaStream_t stream, const LaunchCfg &cfg);
 
 int selftest_wait_timeout(LastResult *last, int limit_ms, cudaStream_t stream, const LaunchCfg &cfg);
+
+// Input validation (validate.cu): ORs the PICO_DEFECT_* bits it finds into
+// *flag (device memory, zeroed by the caller), stream-ordered.
+template <typename Off>
+int launch_validate(const Off *rp, const int *ci, long long n, long long m, unsigned *flag,
+                    cudaStream_t stream, const LaunchCfg &cfg);
 
 // The current device's launch configuration and per-device status record
 // (capi.cu); returns a pico_status.

@@ -75,6 +75,21 @@ def test_argument_checks_need_no_gpu(lib):
     # an empty graph is a no-op
     assert L.pico_coreness(vp(None), vp(None), ctypes.c_int64(0), ctypes.c_int64(0), vp(None),
                            0, vp(None)) == pico.PICO_OK
+    # validation: sizes and pointers are checked on the host; an empty graph
+    # is valid iff it has no arcs, and nothing is read
+    d = ctypes.c_uint32(99)
+    i64 = ctypes.c_int64
+
+    def val(f, rp, ci, n, m):
+        d.value = 99
+        return f(vp(rp), vp(ci), i64(n), i64(m), ctypes.byref(d), vp(None)), d.value
+
+    assert val(L.pico_validate_graph, None, None, -1, 0) == (pico.PICO_ERR_INVALID_ARG, 0)
+    assert val(L.pico_validate_graph, None, None, 0, 0) == (pico.PICO_OK, 0)
+    assert val(L.pico_validate_graph, None, None, 0, 3) == (pico.PICO_ERR_BAD_GRAPH,
+                                                            pico.PICO_DEFECT_ROWS)
+    assert val(L.pico_validate_graph, None, 8, 4, 4)[0] == pico.PICO_ERR_INVALID_ARG
+    assert val(L.pico_validate_graph_i64, 8, None, 4, 4)[0] == pico.PICO_ERR_INVALID_ARG
     # UpdateHisto direction: unknown modes and thresholds outside 1..100
     for mode, pct in ((-1, 25), (3, 25), (pico.PICO_UPDATE_AUTO, 0), (pico.PICO_UPDATE_PULL, 101)):
         assert L.pico_set_histo_update(mode, pct) == pico.PICO_ERR_INVALID_ARG
