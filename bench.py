@@ -321,7 +321,9 @@ def bench_serve(pico, dev, requests: int, plain_requests: int = 2000, loads=(0.5
     stream's length), takes the first `plain_requests` of the same stream.
     All server runs come first, then the plain runs.
     Latency = completion - arrival, host clock, including the host-to-device
-    copy of each CSR and the copy of its result back."""
+    copy of each CSR and the copy of its result back; the device-only latency
+    of a request is the device time of its micro-batch (copies in, launch,
+    copies out), without the wait for admission."""
     import math
     import torch
     import graphgen as gg
@@ -369,16 +371,19 @@ def bench_serve(pico, dev, requests: int, plain_requests: int = 2000, loads=(0.5
         rc = pico.pico_server_drain(srv)
         tk = torch.zeros(count, dtype=torch.int64)
         dn = torch.zeros(count, dtype=torch.int64)
-        k = pico.pico_server_poll(srv, tk, dn, count)
+        dv = torch.zeros(count, dtype=torch.int64)
+        k = pico.pico_server_poll_device(srv, tk, dn, dv, count)
         pico.pico_server_destroy(srv)
         if rc != 0 or k != count:
             raise RuntimeError(f"server failed rc={rc} done={k}")
         arr_t = torch.tensor(arr, dtype=torch.int64)[tk]
         lat = (dn - arr_t).double() / 1e6
         span = (int(dn.max()) - int(torch.tensor(arr).min())) / 1e9
+        dev = dv.double() / 1e6   # the device time of each request's micro-batch
         return {"requests": count, "graphs_per_s": count / span,
                 "p50_ms": float(lat.quantile(0.5)), "p99_ms": float(lat.quantile(0.99)),
-                "mean_ms": float(lat.mean())}
+                "mean_ms": float(lat.mean()),
+                "device_p50_ms": float(dev.quantile(0.5)), "device_p99_ms": float(dev.quantile(0.99))}
 
     pico.pico_set_tuning(*autotune_default())
     run(None, False)   # warm-up: first launches, the memory pool's growth

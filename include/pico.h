@@ -232,6 +232,13 @@ int64_t pico_server_submit(pico_server *server, const int32_t *row_ptr, const in
    (pico_clock_ns) into the arrays; returns how many, or a negative status. */
 int pico_server_poll(pico_server *server, int64_t *tickets, int64_t *done_ns, int cap);
 
+/* The same, and into device_ns (NULL to skip) the device time of the
+   micro-batch that served each request: CUDA events around its copies to
+   the device, its launch and the copies of its results back (-1 when the
+   micro-batch failed). The host-side wait before admission is not in it. */
+int pico_server_poll_device(pico_server *server, int64_t *tickets, int64_t *done_ns,
+                            int64_t *device_ns, int cap);
+
 /* Blocks until every submitted request has completed; returns the first
    error seen by the engine (PICO_OK if none). */
 int pico_server_drain(pico_server *server);

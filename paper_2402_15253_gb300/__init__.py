@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.pico_server_submit.argtypes = [vp, vp, vp, i64, i64, vp, i64]
     L.pico_server_submit.restype = i64
     L.pico_server_poll.argtypes = [vp, vp, vp, i32]
+    L.pico_server_poll_device.argtypes = [vp, vp, vp, vp, i32]
+    L.pico_server_poll_device.restype = i32
     L.pico_server_poll.restype = i32
     L.pico_server_drain.argtypes = [vp]
     L.pico_server_drain.restype = i32
@@ -258,6 +260,11 @@ def pico_server_submit(server, row_ptr, col_idx, n: int, m: int, out_core, arriv
 
 def pico_server_poll(server, tickets, done_ns, cap: int) -> int:
     return load().pico_server_poll(server, _ptr(tickets), _ptr(done_ns), cap)
+
+
+def pico_server_poll_device(server, tickets, done_ns, device_ns, cap: int) -> int:
+    return load().pico_server_poll_device(server, _ptr(tickets), _ptr(done_ns), _ptr(device_ns),
+                                          cap)
 
 
 def pico_server_drain(server) -> int:

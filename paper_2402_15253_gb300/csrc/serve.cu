@@ -15,7 +15,8 @@
 //   completion each micro-batch ends with an event; when it has fired the
 //              results are in the clients' buffers, the memory returns to the
 //              budget and the requests are reported done with their
-//              completion time.
+//              completion time and the micro-batch's device time (events
+//              around its copies in, its launch and its copies out).
 // With single_graph = 1 and max_batch = 1 the engine instead runs one
 // request at a time with the single-graph entry point (the sequential plain
 // path, kept as the baseline).
@@ -54,7 +55,7 @@ struct Batch {
     std::vector<Request> reqs;
     size_t bytes = 0;
     void *dev = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
     int slot = -1;
 };
 
@@ -72,7 +73,7 @@ struct pico_server {
     std::condition_variable cv;
     std::deque<Request> pending;           // submitted, in arrival order
     std::vector<Batch> inflight;
-    std::vector<long long> done_tickets, done_times;
+    std::vector<long long> done_tickets, done_times, done_device;
     size_t inflight_bytes = 0;
     long long next_ticket = 0, submitted = 0, completed = 0;
     int error = PICO_OK;
@@ -94,6 +95,7 @@ struct pico_server {
     int launch(Batch &b)
     {
         cudaStream_t s = streams[b.slot];
+        if (cudaEventRecord(b.start, s) != cudaSuccess) return PICO_ERR_CUDA;
         long long G = (long long)b.reqs.size(), tn = 0, tm = 0;
         long long *h = h_offsets[b.slot];
         h[0] = 0;
@@ -177,13 +179,19 @@ struct pico_server {
                 }
                 if (q != cudaSuccess && error == PICO_OK) error = PICO_ERR_CUDA;
                 const long long t = now_ns();
+                float dev_ms = -1.0f;
+                if (q == cudaSuccess && cudaEventElapsedTime(&dev_ms, b.start, b.done) != cudaSuccess)
+                    dev_ms = -1.0f;
+                const long long dev_ns = dev_ms >= 0.0f ? (long long)(dev_ms * 1e6) : -1;
                 for (const Request &r : b.reqs) {
                     done_tickets.push_back(r.ticket);
                     done_times.push_back(t);
+                    done_device.push_back(dev_ns);
                 }
                 completed += (long long)b.reqs.size();
                 inflight_bytes -= b.bytes;
                 slot_busy[b.slot] = false;
+                cudaEventDestroy(b.start);
                 cudaEventDestroy(b.done);
                 inflight[i] = std::move(inflight.back());
                 inflight.pop_back();
@@ -218,7 +226,8 @@ struct pico_server {
                     b.slot = slot;
                     slot_busy[slot] = true;
                     inflight_bytes += b.bytes;
-                    cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+                    cudaEventCreate(&b.start);   // timed: the device time of the batch
+                    cudaEventCreate(&b.done);
                     lock.unlock();
                     const int rc = launch(b);
                     lock.lock();
@@ -300,7 +309,8 @@ int64_t pico_server_submit(pico_server *s, const int32_t *row_ptr, const int32_t
     return r.ticket;
 }
 
-int pico_server_poll(pico_server *s, int64_t *tickets, int64_t *done_ns, int cap)
+int pico_server_poll_device(pico_server *s, int64_t *tickets, int64_t *done_ns,
+                            int64_t *device_ns, int cap)
 {
     if (!s || cap < 0 || (cap > 0 && (!tickets || !done_ns))) return PICO_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(s->mu);
@@ -308,10 +318,17 @@ int pico_server_poll(pico_server *s, int64_t *tickets, int64_t *done_ns, int cap
     for (int i = 0; i < k; ++i) {
         tickets[i] = s->done_tickets[i];
         done_ns[i] = s->done_times[i];
+        if (device_ns) device_ns[i] = s->done_device[i];
     }
     s->done_tickets.erase(s->done_tickets.begin(), s->done_tickets.begin() + k);
     s->done_times.erase(s->done_times.begin(), s->done_times.begin() + k);
+    s->done_device.erase(s->done_device.begin(), s->done_device.begin() + k);
     return k;
+}
+
+int pico_server_poll(pico_server *s, int64_t *tickets, int64_t *done_ns, int cap)
+{
+    return pico_server_poll_device(s, tickets, done_ns, nullptr, cap);
 }
 
 int pico_server_drain(pico_server *s)

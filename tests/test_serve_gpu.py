@@ -44,10 +44,16 @@ def serve(pico, reqs, algo, budget, streams=4, max_batch=64, single=0, spacing_n
     assert pico.pico_server_drain(srv) == 0
     tk = torch.zeros(len(reqs), dtype=torch.int64)
     dn = torch.zeros(len(reqs), dtype=torch.int64)
-    k = pico.pico_server_poll(srv, tk, dn, len(reqs))
+    dv = torch.zeros(len(reqs), dtype=torch.int64)
+    k = pico.pico_server_poll_device(srv, tk, dn, dv, len(reqs))
     assert k == len(reqs)
     assert sorted(tk.tolist()) == tickets
     assert (dn >= t0).all()
+    # each request's device time (its micro-batch's copies and launch) is
+    # positive and fits between its arrival and its completion (1 ms of
+    # slack between the event clock and the host clock)
+    arrival = t0 + tk * spacing_ns
+    assert (dv > 0).all() and (dv <= dn - arrival + 1_000_000).all()
     assert pico.pico_server_destroy(srv) == 0
     return [out[:g.n].clone().numpy() for g, _, _, out in reqs]
 
